@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs for the core-excitation BSE Hamiltonian.
+
+This module only *draws* inputs: Bloch functions u_nk(x), band energies E_nk,
+the sampled screened core-hole potential W(x, R), the core spin-orbit matrix
+chi, local-basis projections A and short-range couplings M, and start vectors.
+It contains none of the Hamiltonian's arithmetic (no band->grid transform, no
+Fourier transform over k, no Haydock or GMRES step), so both the FP64 CPU
+oracle and the CUDA path can consume the same arrays without sharing code.
+
+Shapes follow the exciton-vector layout psi[alpha][k][n] of Sec. 3.2 (Eq. 8):
+    u      [Nk][Nx][Nb]   complex128, columns orthonormal per k (sum_x |u|^2 = 1)
+    e_nk   [Nk][Nb]       float64, eV
+    chi    [Na][Na]       complex128, eV (Hermitian core spin-orbit, Eq. 4)
+    w_rx   [Nk][Nx]       float64, eV  (W(x, R) of Algorithm 1; R indexed like k)
+    a_proj [Np][Nk][Nb]   complex128   (A^{nu l m}_{n k} of Eq. 14)
+    m_sr   [Na*Np][Na*Np] complex128, eV, index (alpha, p) with alpha slow
+Grid/mesh flattening: k = (m1*nk2 + m2)*nk3 + m3, same for R and for x.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HARTREE_EV = 27.211386245988  # CODATA 2018 Hartree energy in eV
+
+# Configuration ids used in seeds: np.random.default_rng([config_id, site_id, stream_id]).
+STREAM_U, STREAM_E, STREAM_A, STREAM_M, STREAM_B, STREAM_SITE = 1, 2, 3, 4, 5, 6
+
+
+@dataclass
+class BSESystem:
+    n_alpha: int
+    nk: tuple
+    n_bands: int
+    nx: tuple
+    cell: float          # cubic cell side, bohr
+    eps: float           # dielectric constant of the erf model potential
+    u: np.ndarray
+    e_nk: np.ndarray
+    chi: np.ndarray
+    w_rx: np.ndarray
+    a_proj: np.ndarray | None
+    m_sr: np.ndarray | None
+    kshift: tuple = (0.0, 0.0, 0.0)
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_k(self) -> int:
+        return int(np.prod(self.nk))
+
+    @property
+    def n_x(self) -> int:
+        return int(np.prod(self.nx))
+
+    @property
+    def n_proj(self) -> int:
+        return 0 if self.a_proj is None else int(self.a_proj.shape[0])
+
+    @property
+    def dim(self) -> int:
+        return self.n_alpha * self.n_k * self.n_bands
+
+
+# Workload shapes (sizes, cell, screening) of the synthetic stand-ins for the
+# paper's SrTiO3 / Alq3 systems.  "id" seeds the generator.
+CONFIGS = {
+    # 1s edge, single site, validated against dense diagonalisation (N = 128)
+    "k_edge_small": dict(id=1, n_alpha=1, nk=(2, 2, 2), n_bands=16, nx=(8, 8, 8),
+                         cell=7.4, eps=5.0, n_proj=0, so_split=None, m_scale=0.0),
+    # L2,3 edge with multiplets: 6 core states, 8^3 k, 64 bands, 16^3 grid
+    "l23_multiplet": dict(id=2, n_alpha=6, nk=(8, 8, 8), n_bands=64, nx=(16, 16, 16),
+                          cell=7.4, eps=5.0, n_proj=36, so_split=5.7, m_scale=0.5),
+    # SrTiO3 4x4x4-like supercell: 2^3 k, 1024 bands, 48^3 grid
+    "supercell_48": dict(id=4, n_alpha=6, nk=(2, 2, 2), n_bands=1024, nx=(48, 48, 48),
+                         cell=29.5, eps=6.0, n_proj=36, so_split=5.7, m_scale=0.5),
+}
+
+
+def rng_for(config_id: int, site_id: int, stream_id: int) -> np.random.Generator:
+    return np.random.default_rng([int(config_id), int(site_id), int(stream_id)])
+
+
+def complex_normal(rng: np.random.Generator, shape) -> np.ndarray:
+    """Complex normal with unit variance per entry (Re, Im ~ N(0, 1/2))."""
+    s = np.sqrt(0.5)
+    out = np.empty(shape, dtype=np.complex128)
+    out.real = rng.standard_normal(shape) * s
+    out.imag = rng.standard_normal(shape) * s
+    return out
+
+
+def orthonormal_bloch(rng: np.random.Generator, n_k: int, n_x: int, n_bands: int) -> np.ndarray:
+    """u_nk(x) for each k: complex normal (Nx x Nb) with orthonormalised columns.
+
+    Householder QR (numpy.linalg.qr) per k; phases fixed so R has a positive
+    diagonal (makes the draw a deterministic function of the seed).
+    """
+    if n_bands > n_x:
+        raise ValueError("need n_bands <= n_x for orthonormal columns")
+    u = np.empty((n_k, n_x, n_bands), dtype=np.complex128)
+    for k in range(n_k):
+        g = complex_normal(rng, (n_x, n_bands))
+        q, r = np.linalg.qr(g)
+        d = np.diagonal(r)
+        q *= (d / np.abs(d))[None, :]
+        u[k] = q
+    return u
+
+
+def w_erf_hartree(r: np.ndarray, eps: float, a: float = 0.5) -> np.ndarray:
+    """Model screened core-hole potential W(r) = -erf(r/a)/(eps*r) in Hartree.
+
+    At r = 0 the limit -2/(a*sqrt(pi)*eps) is used.
+    """
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    small = r < 1e-12
+    rs = r[~small]
+    from scipy.special import erf
+    out[~small] = -erf(rs / a) / (eps * rs)
+    out[small] = -2.0 / (a * math.sqrt(math.pi) * eps)
+    return out
+
+
+def sample_w(nk, nx, cell: float, eps: float, a: float = 0.5) -> np.ndarray:
+    """W(x, R) in eV on the grid x_j = j*cell/nx and lattice R = r*cell.
+
+    The core sits at the origin; the electron at x + R is taken at the nearest
+    periodic image of the core in the (nk*cell)-periodic supercell
+    (minimum-image convention).  Returns w_rx[R][x].
+    """
+    nk = tuple(int(v) for v in nk)
+    nx = tuple(int(v) for v in nx)
+    axes = []
+    for d in range(3):
+        xs = np.arange(nx[d]) * cell / nx[d]
+        rs = np.arange(nk[d]) * cell
+        pos = rs[:, None] + xs[None, :]          # [R_d][x_d]
+        period = nk[d] * cell
+        pos = np.mod(pos, period)
+        pos = np.minimum(pos, period - pos)
+        axes.append(pos)
+    p0, p1, p2 = axes
+    r2 = (p0[:, None, None, :, None, None] ** 2
+          + p1[None, :, None, None, :, None] ** 2
+          + p2[None, None, :, None, None, :] ** 2)
+    r = np.sqrt(r2).reshape(int(np.prod(nk)), int(np.prod(nx)))
+    return w_erf_hartree(r, eps, a) * HARTREE_EV
+
+
+def spin_orbit_p(split_ev: float) -> np.ndarray:
+    """chi = xi L.S for a p (l = 1) core level in the |m, sigma> basis, eV.
+
+    Basis order alpha = 2*(m + 1) + s, m in (-1, 0, 1), s = 0 (up), 1 (down).
+    The spin-orbit splitting between j = 1/2 and j = 3/2 is 3*xi/2, so
+    xi = 2*split/3.  Eigenvalues: +xi/2 (x4, j = 3/2), -xi (x2, j = 1/2).
+    """
+    xi = 2.0 * split_ev / 3.0
+    ms = (-1, 0, 1)
+    sz = (0.5, -0.5)
+    chi = np.zeros((6, 6), dtype=np.complex128)
+
+    def idx(m, s):
+        return 2 * (m + 1) + s
+
+    for m in ms:
+        for s in (0, 1):
+            chi[idx(m, s), idx(m, s)] += xi * m * sz[s]
+    # (L+ S- + L- S+)/2 ; L+|m> = sqrt(2 - m(m+1))|m+1>, S-|up> = |down>
+    for m in ms:
+        if m < 1:
+            lp = math.sqrt(2 - m * (m + 1))
+            # L+ S- : |m, up> -> |m+1, down>
+            chi[idx(m + 1, 1), idx(m, 0)] += 0.5 * xi * lp
+            chi[idx(m, 0), idx(m + 1, 1)] += 0.5 * xi * lp
+    return chi
+
+
+def random_hermitian(rng: np.random.Generator, n: int, scale: float) -> np.ndarray:
+    g = complex_normal(rng, (n, n))
+    return scale * 0.5 * (g + g.conj().T)
+
+
+def make_system(name: str = "k_edge_small", site: int = 0, *, overrides: dict | None = None,
+                u_dtype=np.complex128) -> BSESystem:
+    """Draw one absorbing site of the named workload shape."""
+    cfg = dict(CONFIGS[name])
+    if overrides:
+        cfg.update(overrides)
+    return make_system_from(cfg, site=site, name=name)
+
+
+def make_system_from(cfg: dict, site: int = 0, name: str = "custom") -> BSESystem:
+    cid = int(cfg.get("id", 99))
+    nk = tuple(int(v) for v in cfg["nk"])
+    nx = tuple(int(v) for v in cfg["nx"])
+    n_k, n_x = int(np.prod(nk)), int(np.prod(nx))
+    nb, na = int(cfg["n_bands"]), int(cfg["n_alpha"])
+    u = orthonormal_bloch(rng_for(cid, site, STREAM_U), n_k, n_x, nb)
+    e_nk = rng_for(cid, site, STREAM_E).uniform(0.0, 20.0, size=(n_k, nb))
+    split = cfg.get("so_split")
+    if na == 6 and split:
+        chi = spin_orbit_p(float(split))
+    else:
+        chi = np.zeros((na, na), dtype=np.complex128)
+    w = sample_w(nk, nx, float(cfg["cell"]), float(cfg["eps"]))
+    if "w_const" in cfg:
+        w = np.full_like(w, float(cfg["w_const"]))
+    np_ = int(cfg.get("n_proj", 0))
+    a_proj = m_sr = None
+    if np_ > 0:
+        ra = rng_for(cid, site, STREAM_A)
+        a = complex_normal(ra, (np_, n_k * nb))
+        a /= np.linalg.norm(a, axis=1, keepdims=True)
+        a_proj = a.reshape(np_, n_k, nb)
+        m_sr = random_hermitian(rng_for(cid, site, STREAM_M), na * np_, float(cfg.get("m_scale", 0.5)))
+    ks = tuple(float(v) for v in cfg.get("kshift", (0.0, 0.0, 0.0)))
+    return BSESystem(n_alpha=na, nk=nk, n_bands=nb, nx=nx, cell=float(cfg["cell"]),
+                     eps=float(cfg["eps"]), u=u, e_nk=e_nk, chi=chi, w_rx=w,
+                     a_proj=a_proj, m_sr=m_sr, kshift=ks, name=name, meta=dict(cfg))
+
+
+def make_start_vectors(sysd: BSESystem, n_vec: int = 1, seed: int = 0) -> np.ndarray:
+    """Start vectors b (dipole-operator stand-in): complex normal, unit norm each.
+
+    Polarisations are independent seeds.  Shape [n_vec][Na*Nk*Nb].
+    """
+    cid = int(sysd.meta.get("id", 99))
+    out = np.empty((n_vec, sysd.dim), dtype=np.complex128)
+    for v in range(n_vec):
+        g = complex_normal(rng_for(cid, 1000 + seed, STREAM_B * 100 + v), (sysd.dim,))
+        out[v] = g / np.linalg.norm(g)
+    return out
+
+
+def omega_grid(n: int = 2000, lo: float = -5.0, hi: float = 30.0) -> np.ndarray:
+    return np.linspace(lo, hi, n)
+
+
+def tiny_system(seed: int, n_alpha=2, nk=(2, 1, 3), n_bands=3, nx=(2, 3, 2), *,
+                n_proj=2, cell=7.4, eps=5.0, kshift=(0.0, 0.0, 0.0),
+                w_const=None, so=True, m_scale=0.5) -> BSESystem:
+    """Small random system with every term present (for oracle self-checks)."""
+    cfg = dict(id=900 + seed, n_alpha=n_alpha, nk=nk, n_bands=n_bands, nx=nx, cell=cell,
+               eps=eps, n_proj=n_proj, so_split=None, m_scale=m_scale, kshift=kshift)
+    if w_const is not None:
+        cfg["w_const"] = w_const
+    s = make_system_from(cfg, site=0, name=f"tiny{seed}")
+    if so:
+        if n_alpha == 6:
+            s.chi = spin_orbit_p(5.7)
+        else:
+            s.chi = random_hermitian(rng_for(900 + seed, 0, STREAM_SITE), n_alpha, 1.0)
+    return s
