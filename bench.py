@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 core-excitation BSE hot path.
+
+One step = one Haydock iteration (Sec. 3.2, Eq. 9) on the L2,3-edge workload
+with multiplets (6 core states, 8^3 k-points, 64 bands, 16^3 grid, 36
+local-basis functions): one application of H (band->grid, k->R x W R->k,
+grid->band, diagonal, spin-orbit, short range) plus the FP64 recursion.
+The metric is H psi matvecs per second.  Inputs are resident in HBM before
+the timed region; u_nk alone is 1.07 GB (complex64-equivalent) > L2, so no
+L2 flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision split_bf16|fp32|fp64]
+  python bench.py --impl reference     # the FP64 CPU oracle on this host's cores
+
+Under torchrun each rank runs an independent replica on its own GPU
+("replicas only": the path has no data exchange); value = all ranks' matvecs
+/ the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BSE H·ψ matvecs/s and GMRES solves/s at spectrum err ≤1e-4 vs FP64 plain"
+WORKLOAD = "l23_multiplet"
+WORKLOAD_DESC = ("L2,3 edge with multiplets: 6 core states (SO split 5.7 eV), k-mesh 8x8x8, Nb=64, "
+                 "grid 16^3, W=-erf(r/0.5)/(5r), 36 local-basis functions, random Hermitian M (0.5 eV)")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default=os.environ.get("BSE_BENCH_PRECISION", "fp32"))
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--cpu-seconds", type=float, default=20.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            bid = f[0].lower()
+            if self.bus_id and not (bid.endswith(self.bus_id[-12:]) or self.bus_id.endswith(bid[-12:])):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel class (one H psi, nc columns)
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(s, prec, n_vec=1):
+    nk, nx, nb, na, npj = s.n_k, s.n_x, s.n_bands, s.n_alpha, s.n_proj
+    nc = na * n_vec
+    u_elem = {"fp64": 16, "fp32": 8, "split_bf16": 8}[prec]     # bytes per complex u_nk(x)
+    phi_elem = 16 if prec == "fp64" else 8
+    vec = nc * nk * nb * 16
+    u = nk * nx * nb * u_elem
+    phi = nk * nx * nc * phi_elem
+    w = nk * nx * (8 if prec == "fp64" else 4)
+    out = {
+        "band_to_grid": u + vec + phi,
+        "kconv": 2 * phi + w,
+        "grid_to_band": u + phi + 2 * vec + npj * nk * nb * 16 + nk * nb * 8,
+    }
+    if prec == "split_bf16":
+        # bf16 hi+lo copies of phi' written by the k-conv and read by grid->band
+        out["kconv"] = phi + nk * nx * nc * 8 + w
+        out["grid_to_band"] = u + nk * nx * nc * 8 + 2 * vec + npj * nk * nb * 16 + nk * nb * 8
+    return out
+
+
+def cpu_oracle_rate(s, b, seconds, max_steps=None):
+    """Haydock steps of the FP64 oracle on this host (untuned), bounded by time."""
+    from oracle import bse_oracle as O
+    import numpy as np
+    v = b / np.linalg.norm(b)
+    vp = np.zeros_like(v)
+    bprev = 0.0
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        w = O.apply_h(s, v)
+        a = float(np.real(np.vdot(v, w)))
+        w = w - a * v - bprev * vp
+        bn = float(np.linalg.norm(w))
+        vp, v, bprev = v, w / bn, bn
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and n >= max_steps):
+            return n, el
+
+
+def reference_arm(args):
+    import numpy as np
+    from paper_1601_07728_gb300 import synth as S
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    s = S.make_system(args.workload)
+    b = S.make_start_vectors(s, 1)[0]
+    cpu_oracle_rate(s, b, 0.0, max_steps=max(1, min(args.warmup, 2)))
+    budget = 90.0
+    n, el = cpu_oracle_rate(s, b, budget, max_steps=args.steps)
+    rate = n / el
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "matvecs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "precision": "fp64 (NumPy/SciPy oracle)"},
+        "cpu_baseline": {"value": rate, "unit": "matvecs/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d FP64 oracle Haydock steps of the full workload (timed steps capped at "
+                                   "%.0f s of CPU time)" % (n, budget)},
+        "e2e": {"value": rate, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    from paper_1601_07728_gb300 import bse, synth as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    s = S.make_system(args.workload)
+    b = S.make_start_vectors(s, 1)[0]
+    stream = torch.cuda.current_stream()
+    sysg = bse.System(s, precision=args.precision, max_vec=1, stream=stream.cuda_stream)
+    n = sysg.dim
+    db = torch.from_numpy(b).to("cuda")
+    K, W = args.steps, args.warmup
+    a_d = torch.zeros(K, dtype=torch.float64, device="cuda")
+    b_d = torch.zeros(K + 1, dtype=torch.float64, device="cuda")
+    st_d = torch.zeros(1, dtype=torch.int32, device="cuda")
+    # warm-up: W Haydock steps
+    sysg.haydock(db, max(W, 1), a=a_d[:max(W, 1)].contiguous(), bcoef=b_d[:max(W, 1) + 1].contiguous(),
+                 steps=st_d)
+    torch.cuda.synchronize()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        try:
+            p = torch.cuda.get_device_properties(local)
+            bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            bus = None
+    clk = ClockSampler(str(bus) if bus else None)
+    clk.start()
+    time.sleep(0.5)
+    sysg.profile(True)
+    l0 = sysg.launches
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sysg.haydock(db, K, a=a_d, bcoef=b_d, steps=st_d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sysg.launches - l0
+    prof = sysg.profile_read()
+    sysg.profile(False)
+    clocks = clk.stop()
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    steps_done = int(st_d.item())
+    value = world * steps_done / (t_max / 1e3)
+
+    # end to end: the public call with pinned host buffers, H2D + D2H every step
+    hp = torch.from_numpy(b).pin_memory()
+    ho = torch.empty_like(hp).pin_memory()
+    hpn, hon = hp.numpy(), ho.numpy()
+    for _ in range(2):
+        sysg.apply_h(hpn, hon)
+    k_e2e = max(10, min(K, 100))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        sysg.apply_h(hpn, hon)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    e2e = world * k_e2e / el
+
+    # roofline of the dominant kernel class
+    peak, peak_kind = peaks()
+    dom = max(("band_to_grid", "kconv", "grid_to_band"), key=lambda k: prof[k][1])
+    nl, tot = prof[dom]
+    alg = algorithmic_bytes(s, args.precision)[dom]
+    avg_s = tot / max(nl, 1) / 1e3
+    achieved = alg / avg_s / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tj = json.load(f)
+        key = "%s/%s/%s" % (args.workload, args.precision, dom)
+        traffic = tj.get(key)
+    except Exception:
+        pass
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            ns, el2 = cpu_oracle_rate(s, b, args.cpu_seconds)
+            cpu = {"value": ns / el2, "unit": "matvecs/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": "%d FP64 NumPy oracle Haydock steps of the same workload (%.1f s; BLAS-threaded "
+                             "matmuls, single-threaded FFTs)" % (ns, el2)}
+        dtype = {"fp64": "f64", "fp32": "f32", "split_bf16": "bf16x3"}[args.precision]
+        line = {
+            "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": t_max / max(steps_done, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "precision": args.precision,
+                       "recursion": "f64 Haydock, no re-orthogonalisation", "n_vec": 1, "dim": n,
+                       "l2": "inputs larger than L2 (u_nk 1.07 GB), no flush", "parallelism": "replicas"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3, "launches": nl},
+            "kernels_ms": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items() if v[0]},
+            "e2e": {"value": e2e, "unit": "matvecs/s", "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16,
+                    "api": "bse_apply_h with pinned host psi/hpsi"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

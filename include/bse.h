@@ -1,0 +1,199 @@
+/*
+ * bse.h -- C ABI of the GB300 core-excitation Bethe-Salpeter hot path.
+ *
+ * The library applies the core-hole / photo-electron BSE Hamiltonian
+ *     H = H_e - H_h - V_D + V_X                          (Sec. 2, Eq. 3)
+ * to exciton vectors psi_{alpha,n,k} (Sec. 3.2, Eq. 8) and drives it inside
+ * the Haydock recursion (Sec. 3.2, Eq. 9) and GMRES for (H - z) x = b with
+ * z = omega + i*Gamma (the resolvent G(omega) = [omega - H]^{-1} of Eq. 2).
+ * H is assembled from
+ *   - diagonal band energies E_nk (Eq. 5) and the core spin-orbit matrix chi
+ *     (Eq. 4), entering as  E_nk psi_{a n k} - sum_b chi_{ab} psi_{b n k};
+ *     the core energy is the energy zero, the lifetime lives in z;
+ *   - the long-range screened direct term W_0 (Sec. 3.2.1, Algorithm 1):
+ *     band->grid sum with e^{ik.x} u_nk(x), k->R Fourier sum (e^{+ik.R},
+ *     unnormalised), multiplication by W(x,R), R->k sum (e^{-ik.R}/Nk) and
+ *     projection back with e^{-ik.x} u*_nk(x).  W is the signed potential
+ *     energy in eV and is added;
+ *   - the short-range direct + exchange term through the local basis of
+ *     Eq. 14 (Sec. 3.2.2): c = (A (x) I_alpha) psi, c' = M c,
+ *     psi' += (A (x) I_alpha)^H c'.
+ *
+ * Conventions
+ *   Vector layout: psi[v][alpha][k][n], n fastest, complex interleaved
+ *   (bse_c128 = {re, im}, identical to numpy / torch complex128).
+ *   Meshes: k index = (m1*nk2 + m2)*nk3 + m3 with k_d = 2*pi*(m_d + s_d)/(nk_d a);
+ *   the lattice vectors R are indexed the same way (R_d = r_d a); the grid
+ *   x index = (j1*nx2 + j2)*nx3 + j3 with x_d = j_d a / nx_d.
+ *   Energies in eV.
+ *
+ * Memory: every array argument of the compute calls may be a host pointer or
+ * a device pointer; the library finds out with cudaPointerGetAttributes and
+ * copies host data in and out on the handle's stream.  Caller buffers are
+ * never freed or retained.  The library owns only the memory of its handles.
+ *
+ * Errors: every call returns a bse_status; no exception or abort crosses the
+ * ABI.  bse_last_error() gives a message for the last failing call on a
+ * handle.  Device-side conditions (Lanczos breakdown, NaN, GMRES not
+ * converged) are collected in device status words and reported after the
+ * call.  Calls on one handle are ordered on the handle's stream and are not
+ * thread-safe against each other.
+ */
+#ifndef BSE_H
+#define BSE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } bse_c128;
+
+typedef enum {
+  BSE_OK = 0,
+  BSE_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, unsupported combination   */
+  BSE_ERR_OOM = 2,           /* device allocation failed                          */
+  BSE_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed                 */
+  BSE_ERR_BREAKDOWN = 4,     /* (not an error) Haydock met an invariant subspace  */
+  BSE_ERR_NOT_CONVERGED = 5, /* GMRES hit max_iter before rtol; best x returned   */
+  BSE_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                      */
+  BSE_ERR_NAN = 7,           /* NaN/Inf met in a recursion coefficient             */
+  BSE_ERR_UNSUPPORTED = 8    /* shape/precision outside what the kernels support   */
+} bse_status;
+
+/* Arithmetic of the band<->grid contractions (Algorithm 1, first and last
+ * lines).  The Haydock / GMRES recursion, inner products, diagonal, spin-orbit
+ * and short-range terms are FP64 in every mode. */
+typedef enum {
+  BSE_PREC_FP64 = 0,        /* u complex128, FP64 FMA: the plain form                 */
+  BSE_PREC_FP32 = 1,        /* u complex64, FP32 FMA, FP32 k-transforms               */
+  BSE_PREC_SPLIT_BF16 = 2   /* u split into bf16 hi+lo, tcgen05 tensor-core MMAs with
+                               3 products (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+} bse_precision;
+
+typedef struct bse_handle bse_handle;
+
+/* Description of one absorbing site.  All pointers are read during
+ * bse_setup only (host or device memory); the caller keeps ownership. */
+typedef struct {
+  int n_alpha;           /* core states Na (1 for a 1s edge, 6 for L2,3)           */
+  int nk[3];             /* k mesh; Nk = nk0*nk1*nk2                               */
+  int n_bands;           /* conduction bands Nb                                     */
+  int nx[3];             /* real-space grid per cell; Nx = nx0*nx1*nx2              */
+  int n_proj;            /* local-basis functions Np (0: no short-range term)      */
+  int max_vec;           /* largest n_vec processed in one pass (0 -> 1); larger
+                            batches are processed in chunks of max_vec            */
+  double kshift[3];      /* mesh shift s_d in units of the k spacing (0 = Gamma)   */
+  const bse_c128* u;     /* [Nk][Nx][Nb] u_nk(x), columns orthonormal per k        */
+  const double* e_nk;    /* [Nk][Nb] band energies, eV                             */
+  const bse_c128* chi;   /* [Na][Na] Hermitian core spin-orbit matrix, eV          */
+  const double* w_rx;    /* [Nk(R)][Nx] sampled W(x, R), eV                         */
+  const bse_c128* a_proj;/* [Np][Nk][Nb] local-basis coefficients A (or NULL)      */
+  const bse_c128* m_sr;  /* [Na*Np][Na*Np] Hermitian couplings, index (alpha,p)
+                            with alpha slow, eV (or NULL)                           */
+  int precision;         /* bse_precision                                           */
+  void* stream;          /* cudaStream_t used by every call on the handle, or NULL */
+} bse_system_desc;
+
+/* Copies the system to the device (current CUDA device), folds e^{ik.x} into
+ * u, converts it to the requested precision and precomputes diag(H).
+ * Sizes: 1 <= Na <= 16, 1 <= Nb <= Nx, nk_d in 1..16, Np in 0..64.
+ * On failure *out is NULL and nothing is leaked. */
+bse_status bse_setup(bse_handle** out, const bse_system_desc* desc);
+
+/* Releases every device buffer of the handle.  NULL is ignored. */
+void bse_destroy(bse_handle* h);
+
+/* Vector length N = Na*Nk*Nb of the handle (0 for NULL). */
+long long bse_dim(const bse_handle* h);
+
+/* hpsi[v] = H psi[v] for v < n_vec, both [n_vec][N] complex128.  psi and hpsi
+ * must not overlap.  Returns when the result is in hpsi (host) or enqueued on
+ * the handle's stream (device output).  One call = n_vec matrix-vector
+ * products (Eq. 9). */
+bse_status bse_apply_h(bse_handle* h, const bse_c128* psi, bse_c128* hpsi, int n_vec);
+
+/* Haydock recursion (Sec. 3.2, Eq. 9) started from b[v] ([n_vec][N]):
+ *   v_0 = b/|b|, b_0 = |b|; w = H v_i; a_i = Re<v_i|w>;
+ *   w -= a_i v_i + b_i v_{i-1}; optional full re-orthogonalisation (classical
+ *   Gram-Schmidt, twice, FP64) against v_0..v_i; b_{i+1} = |w|;
+ *   stop when b_{i+1} <= 1e-12 max(1, |a_i|); v_{i+1} = w / b_{i+1}.
+ * Outputs (host or device): a [n_vec][n_steps], bcoef [n_vec][n_steps+1]
+ * (bcoef[v][0] = |b_v|), steps_done [n_vec].  Entries past steps_done are 0.
+ * All recursion arithmetic is FP64.  Returns BSE_ERR_BREAKDOWN (with valid
+ * outputs) if any vector stopped early, BSE_ERR_NAN on a non-finite
+ * coefficient.  reorth needs n_vec*(n_steps+1)*N*16 bytes of device memory. */
+bse_status bse_haydock(bse_handle* h, const bse_c128* b, int n_vec, int n_steps, int reorth,
+                       double* a, double* bcoef, int* steps_done);
+
+/* Loss function from Haydock coefficients (Eqs. 1-2):
+ *   sigma(omega) = -(1/pi) b_0^2 Im g(omega + i*gamma),
+ *   g(z) = 1/(z - a_0 - b_1^2/(z - a_1 - ... - b_{n-1}^2/(z - a_{n-1} - t))),
+ * t = 0, or (terminator != 0) the constant-chain tail continued with
+ * (a_{n-1}, b_n).  a [n_vec][n_stride], bcoef [n_vec][n_stride+1],
+ * steps [n_vec] (number of a_i used per vector), omega [n_omega],
+ * sigma [n_vec][n_omega].  Evaluated by a device kernel on the current
+ * device's legacy default stream. */
+bse_status bse_cf_spectrum(const double* a, const double* bcoef, const int* steps, int n_vec,
+                           int n_stride, const double* omega, int n_omega, double gamma,
+                           int terminator, double* sigma);
+
+/* Preconditioner choice for bse_gmres. */
+typedef enum { BSE_PRECOND_NONE = 0, BSE_PRECOND_JACOBI = 1 } bse_precond;
+
+/* Restarted right-preconditioned GMRES(restart) for (H - z_j) x_j = b, one
+ * system per complex shift z_j = omega_j + i*Gamma_j, all n_z systems advanced
+ * together (their H applications are batched).  x_0 = 0; Arnoldi by classical
+ * Gram-Schmidt applied twice in FP64; Givens least squares; convergence when
+ * the true residual |b - (H - z)x|/|b| <= rtol (recomputed at each restart and
+ * at exit).  b [N], z [n_z] (bse_c128), x [n_z][N], iters [n_z] (H
+ * applications spent on each system), rel_resid [n_z] (true residual).
+ * Returns BSE_ERR_NOT_CONVERGED if a system hit max_iter.  Needs about
+ * n_z*(restart+3)*N*16 bytes of device memory for the Krylov bases. */
+bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_z, double rtol,
+                     int restart, int max_iter, int precond, bse_c128* x, int* iters,
+                     double* rel_resid);
+
+/* diag(H) [Na][Nk][Nb] (FP64): E_nk - chi_aa + sum_x |u_nk(x)|^2 Wbar(x)
+ * + sum_pq conj(A_p) M_{ap,aq} A_q with Wbar(x) = mean_R W(x,R); the
+ * diagonal of Algorithm 1 plus the short-range term.  Used by the Jacobi
+ * preconditioner. */
+bse_status bse_jacobi_diag(bse_handle* h, double* diag);
+
+/* Number of the library's own kernel launches since the handle was created
+ * (every launch the compute calls enqueue is counted). */
+long long bse_launch_count(const bse_handle* h);
+
+/* Kernel classes timed by the profiling hook below. */
+typedef enum {
+  BSE_K_BAND_TO_GRID = 0,   /* Algorithm 1, first line (band -> grid contraction)     */
+  BSE_K_KCONV = 1,          /* Algorithm 1, lines 3-5 (k->R, x W, R->k)                */
+  BSE_K_GRID_TO_BAND = 2,   /* Algorithm 1, last line + diagonal/spin-orbit/short range */
+  BSE_K_SR_IN = 3,          /* Sec. 3.2.2 projection onto the local basis              */
+  BSE_K_SR_COUPLE = 4,      /* Sec. 3.2.2 multiplet coupling c' = M c                  */
+  BSE_K_PREP = 5,           /* operand preparation for the tensor-core form            */
+  BSE_K_RECURSION = 6,      /* Haydock / GMRES vector kernels (Eq. 9)                  */
+  BSE_K_COUNT = 7
+} bse_kernel_kind;
+
+/* Measurement aid, no counterpart in the paper: when enabled, every kernel
+ * launch of the handle is bracketed by CUDA events on the handle's stream
+ * (a pool of 8192 launches; later launches are not timed).  bse_profile_read
+ * waits for the stream, folds the recorded launches into per-class totals and
+ * returns them for one class; bse_profile_enable(h, 1) also resets them. */
+bse_status bse_profile_enable(bse_handle* h, int enable);
+bse_status bse_profile_read(bse_handle* h, int kind, long long* launches, double* total_ms);
+const char* bse_kernel_name(int kind);
+
+/* Human-readable name of a status code (static storage). */
+const char* bse_status_string(bse_status s);
+
+/* Message of the last failing call on h ("" if none; static text for NULL). */
+const char* bse_last_error(const bse_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSE_H */

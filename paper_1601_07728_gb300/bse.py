@@ -1,0 +1,242 @@
+"""ctypes binding of libbse (include/bse.h): argument marshalling only.
+
+Arrays may be numpy arrays (host) or torch CUDA tensors (device); the
+library itself finds out which and stages host data.  Every step of H psi,
+Haydock, GMRES and the spectrum runs in the library's CUDA kernels; there is
+no Python or CPU fallback: if the library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbse.so")
+
+BSE_OK, BSE_ERR_INVALID_ARG, BSE_ERR_OOM, BSE_ERR_CUDA, BSE_ERR_BREAKDOWN, BSE_ERR_NOT_CONVERGED, \
+    BSE_ERR_TIMEOUT, BSE_ERR_NAN, BSE_ERR_UNSUPPORTED = range(9)
+PREC = {"fp64": 0, "fp32": 1, "split_bf16": 2}
+PRECOND = {"none": 0, "jacobi": 1}
+
+# every function declared in include/bse.h
+EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", "bse_cf_spectrum",
+           "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
+           "bse_profile_enable", "bse_profile_read", "bse_kernel_name"]
+KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("n_alpha", ctypes.c_int),
+        ("nk", ctypes.c_int * 3),
+        ("n_bands", ctypes.c_int),
+        ("nx", ctypes.c_int * 3),
+        ("n_proj", ctypes.c_int),
+        ("max_vec", ctypes.c_int),
+        ("kshift", ctypes.c_double * 3),
+        ("u", ctypes.c_void_p),
+        ("e_nk", ctypes.c_void_p),
+        ("chi", ctypes.c_void_p),
+        ("w_rx", ctypes.c_void_p),
+        ("a_proj", ctypes.c_void_p),
+        ("m_sr", ctypes.c_void_p),
+        ("precision", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_LIB = None
+
+
+def lib():
+    """Load libbse.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbse.so is not built (run paper_1601_07728_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ci, cd, cll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    L.bse_setup.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Desc)]
+    L.bse_setup.restype = ci
+    L.bse_destroy.argtypes = [vp]
+    L.bse_destroy.restype = None
+    L.bse_dim.argtypes = [vp]
+    L.bse_dim.restype = cll
+    L.bse_apply_h.argtypes = [vp, vp, vp, ci]
+    L.bse_apply_h.restype = ci
+    L.bse_haydock.argtypes = [vp, vp, ci, ci, ci, vp, vp, vp]
+    L.bse_haydock.restype = ci
+    L.bse_cf_spectrum.argtypes = [vp, vp, vp, ci, ci, vp, ci, cd, ci, vp]
+    L.bse_cf_spectrum.restype = ci
+    L.bse_gmres.argtypes = [vp, vp, vp, ci, cd, ci, ci, ci, vp, vp, vp]
+    L.bse_gmres.restype = ci
+    L.bse_jacobi_diag.argtypes = [vp, vp]
+    L.bse_jacobi_diag.restype = ci
+    L.bse_launch_count.argtypes = [vp]
+    L.bse_launch_count.restype = cll
+    L.bse_status_string.argtypes = [ci]
+    L.bse_status_string.restype = ctypes.c_char_p
+    L.bse_last_error.argtypes = [vp]
+    L.bse_last_error.restype = ctypes.c_char_p
+    L.bse_profile_enable.argtypes = [vp, ci]
+    L.bse_profile_enable.restype = ci
+    L.bse_profile_read.argtypes = [vp, ci, ctypes.POINTER(cll), ctypes.POINTER(cd)]
+    L.bse_profile_read.restype = ci
+    L.bse_kernel_name.argtypes = [ci]
+    L.bse_kernel_name.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+class BSEError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s %s" % (lib().bse_status_string(status).decode(), msg))
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected numpy array or torch tensor")
+
+
+class System:
+    """One absorbing site on the device (wraps a bse_handle)."""
+
+    def __init__(self, s, precision="fp64", max_vec=1, stream=None):
+        L = lib()
+        self._keep = []
+
+        def host(a, dt):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                self._keep.append(a)
+                return a
+            arr = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(arr)
+            return arr
+
+        d = Desc()
+        d.n_alpha = s.n_alpha
+        d.nk = (ctypes.c_int * 3)(*s.nk)
+        d.n_bands = s.n_bands
+        d.nx = (ctypes.c_int * 3)(*s.nx)
+        d.n_proj = s.n_proj
+        d.max_vec = int(max_vec)
+        d.kshift = (ctypes.c_double * 3)(*s.kshift)
+        d.u = _ptr(host(s.u, np.complex128))
+        d.e_nk = _ptr(host(s.e_nk, np.float64))
+        d.chi = _ptr(host(s.chi, np.complex128))
+        d.w_rx = _ptr(host(s.w_rx, np.float64))
+        d.a_proj = _ptr(host(s.a_proj, np.complex128))
+        d.m_sr = _ptr(host(s.m_sr, np.complex128))
+        d.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        d.stream = stream
+        h = ctypes.c_void_p()
+        st = L.bse_setup(ctypes.byref(h), ctypes.byref(d))
+        self._keep = []
+        if st != BSE_OK:
+            raise BSEError(st, "bse_setup failed")
+        self.h = h
+        self.dim = int(L.bse_dim(h))
+        self.precision = precision
+        self.max_vec = int(max_vec)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, ok=(BSE_OK,)):
+        if st not in ok:
+            raise BSEError(st, lib().bse_last_error(self.h).decode())
+        return st
+
+    @property
+    def launches(self):
+        return int(lib().bse_launch_count(self.h))
+
+    def apply_h(self, psi, out=None):
+        """out = H psi; psi [N] or [V][N] complex128 (numpy or CUDA tensor)."""
+        nv = 1 if psi.ndim == 1 else psi.shape[0]
+        if out is None:
+            out = np.empty_like(psi) if isinstance(psi, np.ndarray) else psi.new_empty(psi.shape)
+        self._check(lib().bse_apply_h(self.h, _ptr(psi), _ptr(out), nv))
+        return out
+
+    def haydock(self, b, n_steps, reorth=False, a=None, bcoef=None, steps=None):
+        """Haydock coefficients (a [V][n], b [V][n+1], steps_done [V], status)."""
+        nv = 1 if b.ndim == 1 else b.shape[0]
+        a = np.zeros((nv, n_steps)) if a is None else a
+        bcoef = np.zeros((nv, n_steps + 1)) if bcoef is None else bcoef
+        steps = np.zeros(nv, dtype=np.int32) if steps is None else steps
+        st = lib().bse_haydock(self.h, _ptr(b), nv, int(n_steps), int(bool(reorth)), _ptr(a), _ptr(bcoef),
+                               _ptr(steps))
+        self._check(st, (BSE_OK, BSE_ERR_BREAKDOWN))
+        return a, bcoef, steps, st
+
+    def gmres(self, b, z, rtol=1e-6, restart=30, max_iter=3000, precond="jacobi", x=None):
+        """Solve (H - z_j) x_j = b for every z_j; returns (x [nz][N], iters, rel_resid, status)."""
+        z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.complex128)
+        nz = z.shape[0]
+        x = np.zeros((nz, self.dim), dtype=np.complex128) if x is None else x
+        iters = np.zeros(nz, dtype=np.int32)
+        rel = np.zeros(nz)
+        st = lib().bse_gmres(self.h, _ptr(b), _ptr(z), nz, float(rtol), int(restart), int(max_iter),
+                             PRECOND[precond] if isinstance(precond, str) else int(precond), _ptr(x),
+                             _ptr(iters), _ptr(rel))
+        self._check(st, (BSE_OK, BSE_ERR_NOT_CONVERGED))
+        return x, iters, rel, st
+
+    def profile(self, enable=True):
+        """Turn per-launch CUDA-event timing on (resets totals) or off."""
+        self._check(lib().bse_profile_enable(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel class: (launches, total ms)} of the timed launches so far."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            n = ctypes.c_longlong()
+            ms = ctypes.c_double()
+            self._check(lib().bse_profile_read(self.h, k, ctypes.byref(n), ctypes.byref(ms)))
+            out[name] = (int(n.value), float(ms.value))
+        return out
+
+    def jacobi_diag(self):
+        d = np.empty(self.dim)
+        self._check(lib().bse_jacobi_diag(self.h, _ptr(d)))
+        return d
+
+
+def cf_spectrum(a, bcoef, steps, omega, gamma, terminator=False):
+    """sigma [V][n_omega] from Haydock coefficients, evaluated by the library's kernel."""
+    a = np.ascontiguousarray(np.atleast_2d(a), dtype=np.float64)
+    bcoef = np.ascontiguousarray(np.atleast_2d(bcoef), dtype=np.float64)
+    steps = np.ascontiguousarray(np.atleast_1d(steps), dtype=np.int32)
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    nv, ns = a.shape
+    sig = np.zeros((nv, omega.size))
+    st = lib().bse_cf_spectrum(_ptr(a), _ptr(bcoef), _ptr(steps), nv, ns, _ptr(omega), omega.size,
+                               float(gamma), int(bool(terminator)), _ptr(sig))
+    if st != BSE_OK:
+        raise BSEError(st, "cf_spectrum failed")
+    return sig

@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of libbse.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bse.h"
+
+#define BSE_MAX_ALPHA 16
+#define BSE_MAX_NK_AXIS 16
+#define BSE_MAX_PROJ 64
+
+// ---------------------------------------------------------------------------
+// complex helpers (interleaved re, im)
+// ---------------------------------------------------------------------------
+template <typename T> struct cvec;
+template <> struct cvec<double> { typedef double2 type; };
+template <> struct cvec<float> { typedef float2 type; };
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(double re, double im);
+template <> __host__ __device__ __forceinline__ double2 cmake<double2>(double re, double im) { return make_double2(re, im); }
+template <> __host__ __device__ __forceinline__ float2 cmake<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+
+// acc += a * b
+template <typename C> __device__ __forceinline__ void cmac(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename C> __device__ __forceinline__ void cmac_conj(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct bse_handle {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  int na = 0, nb = 0, np = 0, prec = 0, max_vec = 1;
+  int nk3[3] = {1, 1, 1}, nx3[3] = {1, 1, 1};
+  int nk = 0, nx = 0;
+  long long N = 0;
+  double kshift[3] = {0, 0, 0};
+
+  // FP64 system data (every precision)
+  double* e_nk = nullptr;     // [Nk][Nb]
+  double2* chi = nullptr;     // [Na][Na]
+  double2* a_proj = nullptr;  // [Np][Nk*Nb]
+  double2* m_sr = nullptr;    // [Na*Np][Na*Np]
+  double* jdiag = nullptr;    // [Na][Nk][Nb]
+  double* twiddle = nullptr;  // [3][16][2] e^{+2 pi i j / nk_d}, j < nk_d
+
+  // band<->grid operands
+  void* u = nullptr;          // FP64: double2 [Nk][Nx][Nb]; FP32: float2; phase folded
+  void* w = nullptr;          // [Nk][Nx] double (FP64) or float
+  __nv_bfloat16* u_hi = nullptr;   // SPLIT_BF16: [Nk][Nx][2Nb] (re, im interleaved)
+  __nv_bfloat16* u_lo = nullptr;
+  __nv_bfloat16* ut_hi = nullptr;  // SPLIT_BF16: [Nk][2Nb][Nx] (transposed copy)
+  __nv_bfloat16* ut_lo = nullptr;
+
+  // scratch sized for max_vec columns
+  void* phi = nullptr;        // [Nk][Nx][Nc] complex (double2 for FP64, float2 otherwise)
+  double2* sr_c = nullptr;    // [max_vec][Na*Np]
+  double2* sr_cp = nullptr;   // [max_vec][Na*Np]
+  __nv_bfloat16* bpsi = nullptr;    // SPLIT_BF16: [Nk][2][Nrow][2Nb] B operand of band->grid
+  __nv_bfloat16* bphi = nullptr;    // SPLIT_BF16: [Nk][2][Nrow][Nx]  B operand of grid->band
+  float* part = nullptr;            // SPLIT_BF16: split-K partial tiles
+  void* tmap = nullptr;             // SPLIT_BF16: tensor maps (device copy)
+  void* tmap_host = nullptr;
+
+  // grow-only device workspace of the Haydock driver (kept between calls)
+  void* ws = nullptr;
+  size_t ws_cap = 0;
+
+  // reusable device staging for host arguments of bse_apply_h
+  void* io_in = nullptr;
+  void* io_out = nullptr;
+  size_t io_cap = 0;
+
+  // profiling hook: event pairs around launches
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;     // 2 per launch
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  long long prof_count[BSE_K_COUNT] = {0};
+  double prof_ms[BSE_K_COUNT] = {0};
+
+  long long launches = 0;
+  std::string err;
+};
+
+// bracket a launch with profiling events (no-op unless enabled)
+void bse_prof_begin(bse_handle* h, int kind);
+void bse_prof_end(bse_handle* h);
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+bool bse_is_device_ptr(const void* p);
+bse_status bse_fail(bse_handle* h, bse_status s, const std::string& msg);
+bse_status bse_cuda_check(bse_handle* h, cudaError_t e, const char* what);
+
+#define BSE_LAUNCHED(h) ((h)->launches++)
+#define BSE_PROF(h, kind, ...)   \
+  do {                           \
+    bse_prof_begin((h), (kind)); \
+    __VA_ARGS__;                 \
+    bse_prof_end(h);             \
+    BSE_LAUNCHED(h);             \
+  } while (0)
+
+// setup kernels (k_setup.cu)
+bse_status bse_setup_device(bse_handle* h, const bse_system_desc* d);
+
+// H psi on device pointers (k_apply.cu); psi/hpsi [n_vec][N] double2, n_vec <= max_vec
+bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, int n_vec);
+
+// tensor-core band<->grid path (k_tc.cu)
+bse_status bse_tc_prepare(bse_handle* h);
+bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec);
+bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec);
+bse_status bse_kconv_bf16(bse_handle* h, int n_vec);
+bse_status bse_tc_status(bse_handle* h);   // device error word of the tensor-core pipeline
+void bse_tc_free(bse_handle* h);
+
+// Krylov drivers (k_krylov.cu)
+bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_steps, int reorth,
+                              double* a, double* bcoef, int* steps_done);
+bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, int n_z, double rtol,
+                            int restart, int max_iter, int precond, double2* x, int* iters,
+                            double* rel_resid);
+bse_status bse_cf_device(const double* a, const double* bcoef, const int* steps, int n_vec,
+                         int n_stride, const double* omega, int n_omega, double gamma,
+                         int terminator, double* sigma, cudaStream_t st);

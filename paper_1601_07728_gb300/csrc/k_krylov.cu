@@ -1,0 +1,671 @@
+// Krylov drivers on the device, all recursion arithmetic in FP64:
+//   Haydock / Lanczos recursion (Sec. 3.2, Eq. 9) with optional classical
+//   Gram-Schmidt re-orthogonalisation, the continued-fraction loss function
+//   (Eqs. 1-2), and restarted right-preconditioned GMRES for (H - z) x = b.
+// Reductions are two-stage and deterministic: fixed per-block partial sums,
+// then one block per vector sums the partials in a fixed tree order.
+#include "bse_internal.cuh"
+
+#include <math.h>
+
+#include <vector>
+
+namespace {
+
+constexpr int RB = 256;      // threads per reduction block
+constexpr int NBLK = 296;    // partial-sum blocks per vector (2 x 148)
+
+enum { ST_BREAKDOWN = 1, ST_NAN = 2 };
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// block-wide sum of a double2 (RB threads)
+__device__ double2 block_sum2(double2 v) {
+  __shared__ double sx[RB], sy[RB];
+  sx[threadIdx.x] = v.x;
+  sy[threadIdx.x] = v.y;
+  __syncthreads();
+  for (int s = RB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sx[threadIdx.x] += sx[threadIdx.x + s];
+      sy[threadIdx.x] += sy[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  double2 r = make_double2(sx[0], sy[0]);
+  __syncthreads();
+  return r;
+}
+
+// partial[v][blk] = sum over the block's slice of conj(x) * y   (y == nullptr: |x|^2)
+// x, y of vector v start at v * xs, v * ys (xs = ys = N for packed batches).
+__global__ void __launch_bounds__(RB) dot_partial_s(const double2* __restrict__ x, long long xs,
+                                                    const double2* __restrict__ y, long long ys,
+                                                    long long N, double2* __restrict__ partial) {
+  const int v = blockIdx.y;
+  const double2* xv = x + (size_t)v * xs;
+  const double2* yv = y ? y + (size_t)v * ys : nullptr;
+  double2 acc = make_double2(0, 0);
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < N; i += (long long)gridDim.x * RB) {
+    double2 a = xv[i];
+    if (yv) {
+      double2 b = yv[i];
+      acc.x += a.x * b.x + a.y * b.y;
+      acc.y += a.x * b.y - a.y * b.x;
+    } else {
+      acc.x += a.x * a.x + a.y * a.y;
+    }
+  }
+  double2 s = block_sum2(acc);
+  if (threadIdx.x == 0) partial[(size_t)v * gridDim.x + blockIdx.x] = s;
+}
+
+// sum of partial[v][0..nblk) in a fixed order
+__device__ double2 sum_partials(const double2* partial, int v, int nblk) {
+  double2 acc = make_double2(0, 0);
+  for (int i = threadIdx.x; i < nblk; i += RB) acc = cadd(acc, partial[(size_t)v * nblk + i]);
+  return block_sum2(acc);
+}
+
+// ---------------------------------------------------------------------------
+// Haydock
+// ---------------------------------------------------------------------------
+// b_0 = |b|; active = (b_0 > 0 and finite)
+__global__ void __launch_bounds__(RB) hay_init_finalize(const double2* partial, int nblk, double* bco,
+                                                        int n_steps, int* active, int* status) {
+  const int v = blockIdx.x;
+  double2 s = sum_partials(partial, v, nblk);
+  if (threadIdx.x == 0) {
+    double b0 = sqrt(s.x);
+    bco[(size_t)v * (n_steps + 1)] = b0;
+    int ok = isfinite(b0) && b0 > 0;
+    active[v] = ok;
+    if (!isfinite(b0)) atomicOr(status, ST_NAN);
+  }
+}
+
+// y[v] = x[v] / bco[v][col]   (only active vectors)
+__global__ void hay_scale(const double2* __restrict__ x, double2* __restrict__ y, long long N,
+                          const double* __restrict__ bco, int col, int stride, const int* __restrict__ active) {
+  const int v = blockIdx.y;
+  if (!active[v]) return;
+  const double inv = 1.0 / bco[(size_t)v * stride + col];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = x[(size_t)v * N + i];
+    y[(size_t)v * N + i] = make_double2(a.x * inv, a.y * inv);
+  }
+}
+
+// a[v][i] = Re <v_i | w>
+__global__ void __launch_bounds__(RB) hay_a_finalize(const double2* partial, int nblk, double* a,
+                                                     int n_steps, int i, const int* active, int* status) {
+  const int v = blockIdx.x;
+  double2 s = sum_partials(partial, v, nblk);
+  if (threadIdx.x == 0 && active[v]) {
+    a[(size_t)v * n_steps + i] = s.x;
+    if (!isfinite(s.x)) atomicOr(status, ST_NAN);
+  }
+}
+
+// w -= a_i v_i + b_i v_{i-1};  partial |w|^2
+__global__ void __launch_bounds__(RB) hay_update(double2* __restrict__ w, const double2* __restrict__ vc,
+                                                 const double2* __restrict__ vp, long long N,
+                                                 const double* __restrict__ a, const double* __restrict__ bco,
+                                                 int n_steps, int i, const int* __restrict__ active,
+                                                 double2* __restrict__ partial) {
+  const int v = blockIdx.y;
+  double2 acc = make_double2(0, 0);
+  if (active[v]) {
+    const double ai = a[(size_t)v * n_steps + i];
+    const double bi = i >= 1 ? bco[(size_t)v * (n_steps + 1) + i] : 0.0;
+    for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < N; e += (long long)gridDim.x * RB) {
+      size_t o = (size_t)v * N + e;
+      double2 ww = w[o], c = vc[o];
+      ww.x -= ai * c.x;
+      ww.y -= ai * c.y;
+      if (i >= 1) {
+        double2 p = vp[o];
+        ww.x -= bi * p.x;
+        ww.y -= bi * p.y;
+      }
+      w[o] = ww;
+      acc.x += ww.x * ww.x + ww.y * ww.y;
+    }
+  }
+  double2 s = block_sum2(acc);
+  if (threadIdx.x == 0) partial[(size_t)v * gridDim.x + blockIdx.x] = s;
+}
+
+// b_{i+1} = |w|; breakdown test; steps_done = i + 1
+__global__ void __launch_bounds__(RB) hay_b_finalize(const double2* partial, int nblk, const double* a,
+                                                     double* bco, int n_steps, int i, int* active,
+                                                     int* steps, int* status) {
+  const int v = blockIdx.x;
+  double2 s = sum_partials(partial, v, nblk);
+  if (threadIdx.x == 0 && active[v]) {
+    double bn = sqrt(s.x);
+    double ai = a[(size_t)v * n_steps + i];
+    bco[(size_t)v * (n_steps + 1) + i + 1] = bn;
+    steps[v] = i + 1;
+    if (!isfinite(bn) || !isfinite(ai)) {
+      active[v] = 0;
+      atomicOr(status, ST_NAN);
+    } else if (bn <= 1e-12 * fmax(1.0, fabs(ai))) {
+      active[v] = 0;
+      atomicOr(status, ST_BREAKDOWN);
+    }
+  }
+}
+
+// h[v][j] partials: <basis[v][j] | w[v]>, grid (nblk, nj, nv)
+__global__ void __launch_bounds__(RB) gs_dot_partial(const double2* __restrict__ basis, long long bstride,
+                                                     const double2* __restrict__ w, long long N,
+                                                     double2* __restrict__ partial) {
+  const int j = blockIdx.y, v = blockIdx.z;
+  const double2* bv = basis + (size_t)v * bstride + (size_t)j * N;
+  const double2* wv = w + (size_t)v * N;
+  double2 acc = make_double2(0, 0);
+  for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < N; e += (long long)gridDim.x * RB) {
+    double2 a = bv[e], b = wv[e];
+    acc.x += a.x * b.x + a.y * b.y;
+    acc.y += a.x * b.y - a.y * b.x;
+  }
+  double2 s = block_sum2(acc);
+  if (threadIdx.x == 0) partial[((size_t)v * gridDim.y + j) * gridDim.x + blockIdx.x] = s;
+}
+
+// coef[v][j] = sum of partials (grid (nj, nv)); optionally accumulated into hacc
+__global__ void __launch_bounds__(RB) gs_dot_finalize(const double2* partial, int nblk, double2* coef,
+                                                      int coef_stride, double2* hacc, int hacc_stride) {
+  const int j = blockIdx.x, v = blockIdx.y;
+  double2 acc = make_double2(0, 0);
+  const double2* p = partial + ((size_t)v * gridDim.x + j) * nblk;
+  for (int i = threadIdx.x; i < nblk; i += RB) acc = cadd(acc, p[i]);
+  double2 s = block_sum2(acc);
+  if (threadIdx.x == 0) {
+    coef[(size_t)v * coef_stride + j] = s;
+    if (hacc) {
+      double2 o = hacc[(size_t)v * hacc_stride + j];
+      hacc[(size_t)v * hacc_stride + j] = cadd(o, s);
+    }
+  }
+}
+
+// w[v] -= sum_j coef[v][j] basis[v][j]   (only where mask[v] != 0, mask may be null)
+__global__ void gs_subtract(const double2* __restrict__ basis, long long bstride, double2* __restrict__ w,
+                            long long N, const double2* __restrict__ coef, int coef_stride, int nj,
+                            const int* __restrict__ mask) {
+  const int v = blockIdx.y;
+  if (mask && !mask[v]) return;
+  const double2* bv = basis + (size_t)v * bstride;
+  const double2* cv = coef + (size_t)v * coef_stride;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    double2 acc = w[(size_t)v * N + e];
+    for (int j = 0; j < nj; ++j) {
+      double2 c = cv[j], b = bv[(size_t)j * N + e];
+      acc.x -= c.x * b.x - c.y * b.y;
+      acc.y -= c.x * b.y + c.y * b.x;
+    }
+    w[(size_t)v * N + e] = acc;
+  }
+}
+
+__global__ void copy_vecs(const double2* __restrict__ src, double2* __restrict__ dst, long long N,
+                          long long dst_stride) {
+  const int v = blockIdx.y;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+    dst[(size_t)v * dst_stride + e] = src[(size_t)v * N + e];
+}
+
+template <typename T>
+bse_status dalloc(bse_handle* h, T** p, size_t bytes, const char* what) {
+  if (cudaMalloc((void**)p, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return bse_fail(h, BSE_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+  }
+  return BSE_OK;
+}
+
+struct Freer {
+  std::vector<void*> ptrs;
+  ~Freer() {
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+  template <typename T> void add(T* p) { ptrs.push_back((void*)p); }
+};
+
+#define TRY(x)                   \
+  do {                           \
+    bse_status _s = (x);         \
+    if (_s != BSE_OK) return _s; \
+  } while (0)
+
+// grid-stride launch shape for elementwise kernels over N per vector
+inline dim3 ew_grid(long long N, int nv) {
+  long long b = (N + 255) / 256;
+  if (b > 1184) b = 1184;
+  return dim3((unsigned)b, (unsigned)nv);
+}
+
+bse_status apply_chunked(bse_handle* h, const double2* in, double2* out, int n_vec) {
+  for (int v0 = 0; v0 < n_vec; v0 += h->max_vec) {
+    int nv = n_vec - v0 < h->max_vec ? n_vec - v0 : h->max_vec;
+    TRY(bse_apply_device(h, in + (size_t)v0 * h->N, out + (size_t)v0 * h->N, nv));
+  }
+  return BSE_OK;
+}
+
+// CGS2: for pass in 0,1: coef = basis^H w; w -= basis coef; hacc += coef.
+bse_status cgs2(bse_handle* h, const double2* basis, long long bstride, double2* w, int nv, int nj,
+                double2* partial, double2* coef, int coef_stride, double2* hacc, int hacc_stride,
+                const int* mask) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  for (int pass = 0; pass < 2; ++pass) {
+    BSE_PROF(h, BSE_K_RECURSION, gs_dot_partial<<<dim3(NBLK, nj, nv), RB, 0, st>>>(basis, bstride, w, N, partial));
+    BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, NBLK, coef, coef_stride, hacc, hacc_stride));
+    BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask));
+  }
+  return BSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// continued fraction  (Eqs. 1-2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 csqrt_(double2 a) {
+  double r = hypot(a.x, a.y);
+  double re = sqrt(fmax(0.5 * (r + a.x), 0.0));
+  double im = sqrt(fmax(0.5 * (r - a.x), 0.0));
+  return make_double2(re, a.y < 0 ? -im : im);
+}
+
+__global__ void cf_kernel(const double* __restrict__ a, const double* __restrict__ bco,
+                          const int* __restrict__ steps, int n_stride, const double* __restrict__ omega,
+                          int n_omega, double gamma, int terminator, double* __restrict__ sigma) {
+  const int v = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_omega) return;
+  const double* av = a + (size_t)v * n_stride;
+  const double* bv = bco + (size_t)v * (n_stride + 1);
+  const int n = steps[v];
+  if (n <= 0) {
+    sigma[(size_t)v * n_omega + j] = 0.0;
+    return;
+  }
+  const double2 z = make_double2(omega[j], gamma);
+  double2 t = make_double2(0, 0);
+  if (terminator && bv[n] > 0) {
+    const double binf = bv[n], b2 = binf * binf;
+    double2 zz = make_double2(z.x - av[n - 1], z.y);
+    double2 disc = make_double2(zz.x * zz.x - zz.y * zz.y - 4 * b2, 2 * zz.x * zz.y);
+    double2 r = csqrt_(disc);
+    double2 g1 = make_double2((zz.x - r.x) / (2 * b2), (zz.y - r.y) / (2 * b2));
+    double2 g2 = make_double2((zz.x + r.x) / (2 * b2), (zz.y + r.y) / (2 * b2));
+    double2 g = g1.y <= 0 ? g1 : g2;
+    t = make_double2(b2 * g.x, b2 * g.y);
+  }
+  double2 d = make_double2(z.x - av[n - 1] - t.x, z.y - t.y);
+  for (int i = n - 2; i >= 0; --i) {
+    double bb = bv[i + 1] * bv[i + 1];
+    double2 q = cdiv(make_double2(bb, 0), d);
+    d = make_double2(z.x - av[i] - q.x, z.y - q.y);
+  }
+  double2 g = cdiv(make_double2(1, 0), d);
+  sigma[(size_t)v * n_omega + j] = -(bv[0] * bv[0]) / M_PI * g.y;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES helpers.  Hessenberg per system stored column-major: Hs[v][j][i] =
+// H(i, j), (m+1) rows per column, so the Gram-Schmidt coefficients of column j
+// accumulate into a contiguous slice.
+// ---------------------------------------------------------------------------
+// r = b - (W - z x) = b - W + z x   (W = H x); r written to V_0 of each system
+__global__ void gm_residual(const double2* __restrict__ b, const double2* __restrict__ W,
+                            const double2* __restrict__ x, const double2* __restrict__ z,
+                            double2* __restrict__ V, long long vstride, long long N, int first) {
+  const int v = blockIdx.y;
+  const double2 zv = z[v];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    size_t o = (size_t)v * N + e;
+    double2 bb = b[e];
+    if (first) {
+      V[(size_t)v * vstride + e] = bb;
+    } else {
+      double2 xx = x[o], ww = W[o];
+      V[(size_t)v * vstride + e] =
+          make_double2(bb.x - ww.x + zv.x * xx.x - zv.y * xx.y, bb.y - ww.y + zv.x * xx.y + zv.y * xx.x);
+    }
+  }
+}
+
+// beta = |r|, rel = beta/|b|; active = rel > rtol && iters < max_iter; g = [beta, 0...]
+__global__ void __launch_bounds__(RB) gm_beta(const double2* partial, int nblk, double bnorm, double rtol,
+                                              int max_iter, const int* iters, double* beta, double* rel,
+                                              int* active, double2* g, int m) {
+  const int v = blockIdx.x;
+  double2 s = sum_partials(partial, v, nblk);
+  if (threadIdx.x == 0) {
+    double bt = sqrt(s.x);
+    beta[v] = bt;
+    rel[v] = bt / bnorm;
+    active[v] = (bt / bnorm > rtol) && (iters[v] < max_iter) && isfinite(bt);
+    for (int i = 0; i <= m; ++i) g[(size_t)v * (m + 1) + i] = make_double2(i == 0 ? bt : 0.0, 0.0);
+  }
+}
+
+// T = P V_j (Jacobi: P = 1/(d - z); none: identity)
+__global__ void gm_precond(const double2* __restrict__ V, long long vstride, double2* __restrict__ T,
+                           long long N, const double* __restrict__ d, const double2* __restrict__ z,
+                           int jacobi) {
+  const int v = blockIdx.y;
+  const double2 zv = z[v];
+  const double2* vv = V + (size_t)v * vstride;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    double2 a = vv[e];
+    if (jacobi) a = cdiv(a, make_double2(d[e] - zv.x, -zv.y));
+    T[(size_t)v * N + e] = a;
+  }
+}
+
+// W -= z T
+__global__ void gm_shift(double2* __restrict__ W, const double2* __restrict__ T, const double2* __restrict__ z,
+                         long long N) {
+  const int v = blockIdx.y;
+  const double2 zv = z[v];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    size_t o = (size_t)v * N + e;
+    double2 t = T[o], w = W[o];
+    W[o] = make_double2(w.x - (zv.x * t.x - zv.y * t.y), w.y - (zv.x * t.y + zv.y * t.x));
+  }
+}
+
+#define HS(H, i, j) (H)[(size_t)(j) * (m + 1) + (i)]
+
+// H(j+1, j) = |w|; Givens update of column j; estimated residual; iteration count.
+__global__ void __launch_bounds__(RB) gm_givens(const double2* partial, int nblk, double2* Hs, double* cs,
+                                                double2* sn, double2* g, double* hnorm, int m, int j,
+                                                double bnorm, double rtol, int max_iter, int* active,
+                                                int* iters, int* jdone, double* est) {
+  const int v = blockIdx.x;
+  double2 s = sum_partials(partial, v, nblk);
+  if (threadIdx.x != 0 || !active[v]) return;
+  double hn = sqrt(s.x);
+  hnorm[v] = hn;
+  double2* H = Hs + (size_t)v * (m + 1) * m;
+  double* c = cs + (size_t)v * m;
+  double2* sv = sn + (size_t)v * m;
+  double2* gv = g + (size_t)v * (m + 1);
+  HS(H, j + 1, j) = make_double2(hn, 0);
+  for (int i = 0; i < j; ++i) {
+    double2 h0 = HS(H, i, j), h1 = HS(H, i + 1, j);
+    double2 si = sv[i];
+    // t1 = c h0 + s h1 ; t2 = -conj(s) h0 + c h1
+    double2 t1 = make_double2(c[i] * h0.x + si.x * h1.x - si.y * h1.y, c[i] * h0.y + si.x * h1.y + si.y * h1.x);
+    double2 t2 = make_double2(-(si.x * h0.x + si.y * h0.y) + c[i] * h1.x, -(si.x * h0.y - si.y * h0.x) + c[i] * h1.y);
+    HS(H, i, j) = t1;
+    HS(H, i + 1, j) = t2;
+  }
+  double2 aa = HS(H, j, j), bb = HS(H, j + 1, j);
+  double na_ = hypot(aa.x, aa.y), nb_ = hypot(bb.x, bb.y);
+  double rr = hypot(na_, nb_);
+  if (na_ == 0.0) {
+    c[j] = 0.0;
+    sv[j] = make_double2(1, 0);
+    HS(H, j, j) = bb;
+  } else {
+    double2 ph = make_double2(aa.x / na_, aa.y / na_);
+    c[j] = na_ / rr;
+    sv[j] = make_double2((ph.x * bb.x + ph.y * bb.y) / rr, (ph.y * bb.x - ph.x * bb.y) / rr);  // ph conj(bb)/rr
+    HS(H, j, j) = make_double2(ph.x * rr, ph.y * rr);
+  }
+  HS(H, j + 1, j) = make_double2(0, 0);
+  double2 gj = gv[j], sj = sv[j];
+  gv[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));  // -conj(s) g_j
+  gv[j] = make_double2(c[j] * gj.x, c[j] * gj.y);
+  iters[v] += 1;
+  jdone[v] = j + 1;
+  double e = hypot(gv[j + 1].x, gv[j + 1].y) / bnorm;
+  est[v] = e;
+  if (e <= rtol || iters[v] >= max_iter || hn == 0.0 || !isfinite(e)) active[v] = 0;
+}
+
+// V_{j+1} = w / |w| for systems still active after column j
+__global__ void gm_next(const double2* w, long long wstride, double2* V, long long vstride, long long N,
+                        const double* __restrict__ hnorm, const int* __restrict__ mask) {
+  const int v = blockIdx.y;
+  if (!mask[v] || !(hnorm[v] > 0)) return;
+  const double inv = 1.0 / hnorm[v];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    double2 a = w[(size_t)v * wstride + e];
+    V[(size_t)v * vstride + e] = make_double2(a.x * inv, a.y * inv);
+  }
+}
+
+// back substitution y = R^{-1} g over the system's own jdone columns
+__global__ void gm_solve(const double2* Hs, const double2* g, double2* y, const int* jdone, int m, int nz) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nz) return;
+  const double2* H = Hs + (size_t)v * (m + 1) * m;
+  const double2* gv = g + (size_t)v * (m + 1);
+  double2* yv = y + (size_t)v * m;
+  const int nj = jdone[v];
+  for (int i = nj - 1; i >= 0; --i) {
+    double2 acc = gv[i];
+    for (int k = i + 1; k < nj; ++k) {
+      double2 hk = HS(H, i, k), yk = yv[k];
+      acc.x -= hk.x * yk.x - hk.y * yk.y;
+      acc.y -= hk.x * yk.y + hk.y * yk.x;
+    }
+    yv[i] = cdiv(acc, HS(H, i, i));
+  }
+  for (int i = nj; i < m; ++i) yv[i] = make_double2(0, 0);
+}
+
+// x += P (V y)
+__global__ void gm_update_x(const double2* __restrict__ V, long long vstride, const double2* __restrict__ y,
+                            const int* __restrict__ jdone, int m, double2* __restrict__ x, long long N,
+                            const double* __restrict__ d, const double2* __restrict__ z, int jacobi) {
+  const int v = blockIdx.y;
+  const int nj = jdone[v];
+  if (nj <= 0) return;
+  const double2* vv = V + (size_t)v * vstride;
+  const double2* yv = y + (size_t)v * m;
+  const double2 zv = z[v];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    double2 acc = make_double2(0, 0);
+    for (int j = 0; j < nj; ++j) {
+      double2 a = vv[(size_t)j * N + e], c = yv[j];
+      acc.x += c.x * a.x - c.y * a.y;
+      acc.y += c.x * a.y + c.y * a.x;
+    }
+    if (jacobi) acc = cdiv(acc, make_double2(d[e] - zv.x, -zv.y));
+    double2 o = x[(size_t)v * N + e];
+    x[(size_t)v * N + e] = make_double2(o.x + acc.x, o.y + acc.y);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_steps, int reorth,
+                              double* a_d, double* b_d, int* steps_d) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  Freer fr;
+  double2 *v3 = nullptr, *partial = nullptr, *basis = nullptr, *coef = nullptr;
+  int *active = nullptr, *status = nullptr;
+  {
+    // three vectors, partial sums, flags: one grow-only workspace kept by the handle
+    const size_t bv = 3 * (size_t)n_vec * N * sizeof(double2);
+    const size_t bp = (size_t)n_vec * NBLK * sizeof(double2);
+    const size_t need = bv + bp + 256 + (size_t)n_vec * sizeof(int) + 256;
+    if (h->ws_cap < need) {
+      if (h->ws) cudaFree(h->ws);
+      h->ws = nullptr;
+      h->ws_cap = 0;
+      TRY(dalloc(h, (char**)&h->ws, need, "haydock workspace"));
+      h->ws_cap = need;
+    }
+    char* p = (char*)h->ws;
+    v3 = (double2*)p;
+    partial = (double2*)(p + bv);
+    status = (int*)(p + bv + bp);
+    active = (int*)(p + bv + bp + 256);
+  }
+  if (reorth) {
+    TRY(dalloc(h, &partial, (size_t)n_vec * NBLK * (n_steps + 1) * sizeof(double2), "gs partials"));
+    fr.add(partial);
+    TRY(dalloc(h, &basis, (size_t)n_vec * (n_steps + 1) * N * sizeof(double2), "re-orthogonalisation basis"));
+    fr.add(basis);
+    TRY(dalloc(h, &coef, (size_t)n_vec * (n_steps + 1) * sizeof(double2), "gs coefficients"));
+    fr.add(coef);
+  }
+  cudaMemsetAsync(a_d, 0, (size_t)n_vec * n_steps * sizeof(double), st);
+  cudaMemsetAsync(b_d, 0, (size_t)n_vec * (n_steps + 1) * sizeof(double), st);
+  cudaMemsetAsync(steps_d, 0, n_vec * sizeof(int), st);
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  double2* buf[3] = {v3, v3 + (size_t)n_vec * N, v3 + 2 * (size_t)n_vec * N};
+  double2 *vp = buf[0], *vc = buf[1], *w = buf[2];
+  const dim3 eg = ew_grid(N, n_vec);
+  // v_0 = b / |b|
+  BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(b, N, nullptr, 0, N, partial));
+  BSE_PROF(h, BSE_K_RECURSION, hay_init_finalize<<<n_vec, RB, 0, st>>>(partial, NBLK, b_d, n_steps, active, status));
+  BSE_PROF(h, BSE_K_RECURSION, hay_scale<<<eg, 256, 0, st>>>(b, vc, N, b_d, 0, n_steps + 1, active));
+  if (reorth) {
+    BSE_PROF(h, BSE_K_RECURSION, copy_vecs<<<eg, 256, 0, st>>>(vc, basis, N, (long long)(n_steps + 1) * N));
+  }
+  for (int i = 0; i < n_steps; ++i) {
+    TRY(apply_chunked(h, vc, w, n_vec));                       // w = H v_i
+    BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(vc, N, w, N, N, partial));
+    BSE_PROF(h, BSE_K_RECURSION, hay_a_finalize<<<n_vec, RB, 0, st>>>(partial, NBLK, a_d, n_steps, i, active, status));
+    BSE_PROF(h, BSE_K_RECURSION, hay_update<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, vc, vp, N, a_d, b_d, n_steps, i, active, partial));
+    if (reorth) {
+      TRY(cgs2(h, basis, (long long)(n_steps + 1) * N, w, n_vec, i + 1, partial, coef, n_steps + 1,
+               nullptr, 0, active));
+      BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, N, nullptr, 0, N, partial));
+    }
+    BSE_PROF(h, BSE_K_RECURSION, hay_b_finalize<<<n_vec, RB, 0, st>>>(partial, NBLK, a_d, b_d, n_steps, i, active, steps_d, status));
+    hay_scale<<<eg, 256, 0, st>>>(w, w, N, b_d, i + 1, n_steps + 1, active);   // v_{i+1}
+    BSE_LAUNCHED(h);
+    if (reorth && i + 1 <= n_steps) {
+      BSE_PROF(h, BSE_K_RECURSION, copy_vecs<<<eg, 256, 0, st>>>(w, basis + (size_t)(i + 1) * N, N, (long long)(n_steps + 1) * N));
+    }
+    double2* t = vp;
+    vp = vc;
+    vc = w;
+    w = t;
+  }
+  TRY(bse_cuda_check(h, cudaGetLastError(), "haydock kernels"));
+  int hs = 0;
+  TRY(bse_cuda_check(h, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st), "status copy"));
+  TRY(bse_cuda_check(h, cudaStreamSynchronize(st), "haydock sync"));
+  if (hs & ST_NAN) return bse_fail(h, BSE_ERR_NAN, "non-finite Haydock coefficient");
+  if (hs & ST_BREAKDOWN) return BSE_ERR_BREAKDOWN;
+  return BSE_OK;
+}
+
+bse_status bse_cf_device(const double* a, const double* bcoef, const int* steps, int n_vec, int n_stride,
+                         const double* omega, int n_omega, double gamma, int terminator, double* sigma,
+                         cudaStream_t st) {
+  dim3 g((unsigned)((n_omega + 127) / 128), (unsigned)n_vec);
+  cf_kernel<<<g, 128, 0, st>>>(a, bcoef, steps, n_stride, omega, n_omega, gamma, terminator, sigma);
+  return cudaGetLastError() == cudaSuccess ? BSE_OK : BSE_ERR_CUDA;
+}
+
+bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, int n_z, double rtol,
+                            int restart, int max_iter, int precond, double2* x, int* iters_d,
+                            double* rel_d) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  const int m = restart;
+  const int jac = precond == BSE_PRECOND_JACOBI;
+  Freer fr;
+  double2 *V, *T, *W, *partial, *Hs, *sn, *g, *y, *coef;
+  double *cs, *beta, *hnorm, *est;
+  int *active, *jdone, *mask;
+  const long long vstride = (long long)(m + 1) * N;
+  TRY(dalloc(h, &V, (size_t)n_z * vstride * sizeof(double2), "krylov basis")); fr.add(V);
+  TRY(dalloc(h, &T, (size_t)n_z * N * sizeof(double2), "gmres T")); fr.add(T);
+  TRY(dalloc(h, &W, (size_t)n_z * N * sizeof(double2), "gmres W")); fr.add(W);
+  TRY(dalloc(h, &partial, (size_t)n_z * NBLK * (m + 1) * sizeof(double2), "partials")); fr.add(partial);
+  TRY(dalloc(h, &Hs, (size_t)n_z * (m + 1) * m * sizeof(double2), "hessenberg")); fr.add(Hs);
+  TRY(dalloc(h, &sn, (size_t)n_z * m * sizeof(double2), "givens s")); fr.add(sn);
+  TRY(dalloc(h, &g, (size_t)n_z * (m + 1) * sizeof(double2), "givens g")); fr.add(g);
+  TRY(dalloc(h, &y, (size_t)n_z * m * sizeof(double2), "y")); fr.add(y);
+  TRY(dalloc(h, &coef, (size_t)n_z * (m + 1) * sizeof(double2), "coef")); fr.add(coef);
+  TRY(dalloc(h, &cs, (size_t)n_z * m * sizeof(double), "givens c")); fr.add(cs);
+  TRY(dalloc(h, &beta, (size_t)n_z * sizeof(double), "beta")); fr.add(beta);
+  TRY(dalloc(h, &hnorm, (size_t)n_z * sizeof(double), "hnorm")); fr.add(hnorm);
+  TRY(dalloc(h, &est, (size_t)n_z * sizeof(double), "est")); fr.add(est);
+  TRY(dalloc(h, &active, (size_t)n_z * sizeof(int), "active")); fr.add(active);
+  TRY(dalloc(h, &jdone, (size_t)n_z * sizeof(int), "jdone")); fr.add(jdone);
+  TRY(dalloc(h, &mask, (size_t)n_z * sizeof(int), "mask")); fr.add(mask);
+
+  double bnorm = 0;
+  {
+    BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, 1), RB, 0, st>>>(b, N, nullptr, 0, N, partial));
+    std::vector<double2> hp(NBLK);
+    TRY(bse_cuda_check(h, cudaMemcpyAsync(hp.data(), partial, NBLK * sizeof(double2), cudaMemcpyDeviceToHost, st), "bnorm"));
+    TRY(bse_cuda_check(h, cudaStreamSynchronize(st), "bnorm sync"));
+    for (int i = 0; i < NBLK; ++i) bnorm += hp[i].x;
+    bnorm = sqrt(bnorm);
+  }
+  if (!(bnorm > 0) || !isfinite(bnorm)) return bse_fail(h, BSE_ERR_INVALID_ARG, "b must be nonzero and finite");
+  cudaMemsetAsync(x, 0, (size_t)n_z * N * sizeof(double2), st);
+  cudaMemsetAsync(iters_d, 0, n_z * sizeof(int), st);
+  const dim3 eg = ew_grid(N, n_z);
+  std::vector<int> hact(n_z);
+  for (int cycle = 0;; ++cycle) {
+    // true residual r = b - (H - z) x into V_0, |r|, activity
+    if (cycle > 0) TRY(apply_chunked(h, x, W, n_z));
+    BSE_PROF(h, BSE_K_RECURSION, gm_residual<<<eg, 256, 0, st>>>(b, W, x, z, V, vstride, N, cycle == 0));
+    BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_z), RB, 0, st>>>(V, vstride, nullptr, 0, N, partial));
+    BSE_PROF(h, BSE_K_RECURSION, gm_beta<<<n_z, RB, 0, st>>>(partial, NBLK, bnorm, rtol, max_iter, iters_d, beta, rel_d, active, g, m));
+    TRY(bse_cuda_check(h, cudaMemcpyAsync(hact.data(), active, n_z * sizeof(int), cudaMemcpyDeviceToHost, st), "active copy"));
+    TRY(bse_cuda_check(h, cudaStreamSynchronize(st), "gmres sync"));
+    int nact = 0;
+    for (int v = 0; v < n_z; ++v) nact += hact[v];
+    if (nact == 0) break;
+    cudaMemsetAsync(jdone, 0, n_z * sizeof(int), st);
+    cudaMemsetAsync(Hs, 0, (size_t)n_z * (m + 1) * m * sizeof(double2), st);
+    cudaMemsetAsync(hnorm, 0, n_z * sizeof(double), st);
+    // V_0 = r / beta (in place)
+    BSE_PROF(h, BSE_K_RECURSION, gm_next<<<eg, 256, 0, st>>>(V, vstride, V, vstride, N, beta, active));
+    for (int j = 0; j < m; ++j) {
+      cudaMemcpyAsync(mask, active, n_z * sizeof(int), cudaMemcpyDeviceToDevice, st);
+      BSE_PROF(h, BSE_K_RECURSION, gm_precond<<<eg, 256, 0, st>>>(V + (size_t)j * N, vstride, T, N, h->jdiag, z, jac));
+      TRY(apply_chunked(h, T, W, n_z));
+      BSE_PROF(h, BSE_K_RECURSION, gm_shift<<<eg, 256, 0, st>>>(W, T, z, N));
+      TRY(cgs2(h, V, vstride, W, n_z, j + 1, partial, coef, m + 1, Hs + (size_t)j * (m + 1),
+               (m + 1) * m, mask));
+      BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_z), RB, 0, st>>>(W, N, nullptr, 0, N, partial));
+      BSE_PROF(h, BSE_K_RECURSION, gm_givens<<<n_z, RB, 0, st>>>(partial, NBLK, Hs, cs, sn, g, hnorm, m, j, bnorm, rtol, max_iter,
+                                   active, iters_d, jdone, est));
+      if (j + 1 < m) {
+        BSE_PROF(h, BSE_K_RECURSION, gm_next<<<eg, 256, 0, st>>>(W, N, V + (size_t)(j + 1) * N, vstride, N, hnorm, active));
+      }
+      TRY(bse_cuda_check(h, cudaMemcpyAsync(hact.data(), active, n_z * sizeof(int), cudaMemcpyDeviceToHost, st), "active copy"));
+      TRY(bse_cuda_check(h, cudaStreamSynchronize(st), "gmres sync"));
+      nact = 0;
+      for (int v = 0; v < n_z; ++v) nact += hact[v];
+      if (nact == 0) break;
+    }
+    BSE_PROF(h, BSE_K_RECURSION, gm_solve<<<(n_z + 127) / 128, 128, 0, st>>>(Hs, g, y, jdone, m, n_z));
+    BSE_PROF(h, BSE_K_RECURSION, gm_update_x<<<eg, 256, 0, st>>>(V, vstride, y, jdone, m, x, N, h->jdiag, z, jac));
+  }
+  TRY(bse_cuda_check(h, cudaGetLastError(), "gmres kernels"));
+  std::vector<int> hit(n_z);
+  std::vector<double> hrel(n_z);
+  TRY(bse_cuda_check(h, cudaMemcpyAsync(hit.data(), iters_d, n_z * sizeof(int), cudaMemcpyDeviceToHost, st), "iters"));
+  TRY(bse_cuda_check(h, cudaMemcpyAsync(hrel.data(), rel_d, n_z * sizeof(double), cudaMemcpyDeviceToHost, st), "rel"));
+  TRY(bse_cuda_check(h, cudaStreamSynchronize(st), "gmres end"));
+  for (int v = 0; v < n_z; ++v)
+    if (!(hrel[v] <= rtol)) return BSE_ERR_NOT_CONVERGED;
+  return BSE_OK;
+}

@@ -1,0 +1,758 @@
+// Split-bf16 tensor-core form of Algorithm 1 (Sec. 3.2.1) on sm_103a.
+//
+// Both band<->grid contractions are real GEMMs on the re/im-interleaved
+// Bloch functions U~ (U = e^{ik.x} u):
+//   band->grid (first line):  Phi_k[x][j]  = sum_q U~_k[x][q] Bpsi_k[j][q]
+//       q = 2n + u (u = re/im part of U), j = 2c + s (s = re/im part of phi_c),
+//       Bpsi holds (psi_r, -psi_i) for s = 0 and (psi_i, psi_r) for s = 1.
+//   grid->band (last line):   D_k[q][j] = sum_x U~_k[x][q] Phi'_k[x][j]
+//       psi'_{c,n} = (D[2n][2c] + D[2n+1][2c+1]) + i (D[2n][2c+1] - D[2n+1][2c]).
+// Every operand is split v = hi + lo into two bf16 numbers and each product
+// is formed as hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
+//
+// tc_gemm is a persistent warp-specialised kernel: warp 0 streams 128 x 64
+// operand tiles with TMA (128-byte swizzle) into a ring of shared-memory
+// stages, warp 1 issues tcgen05.mma (M = 128, N = 16..256, K = 16) from one
+// thread into double-buffered TMEM accumulators, warps 2-5 drain TMEM with
+// tcgen05.ld and write the results.  Every mbarrier wait is bounded in time;
+// on timeout the kernel records an error word, drains its own copies and
+// frees its TMEM before returning.
+#include "bse_internal.cuh"
+
+#include <cuda.h>
+#include <stdio.h>
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_KB = 64;                  // bf16 per K block = one 128-byte swizzle row
+constexpr int TC_THREADS = 192;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
+constexpr int SMEM_BUDGET = 224 * 1024;
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false on timeout or abort.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(a, parity)) return true;
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtime() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          dst),
+      "l"((unsigned long long)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, unsigned long long adesc, unsigned long long bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// 32 TMEM lanes (this warp's quadrant) x 16 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (tcgen05 descriptor version 1).
+__device__ __forceinline__ unsigned long long sdesc_sw128(uint32_t saddr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+  d |= (unsigned long long)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (unsigned long long)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+  d |= (unsigned long long)1 << 46;                 // descriptor version
+  d |= (unsigned long long)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// persistent split-bf16 GEMM
+// ---------------------------------------------------------------------------
+struct TcParams {
+  int mode;            // 0: band->grid (phi out), 1: grid->band (split-K partials out)
+  int ntiles;          // work units = batch * mtiles * nsplit
+  int mtiles, nsplit;
+  int kb_per_split, kb_total;
+  int nn;              // MMA N (multiple of 16)
+  int stages;
+  uint32_t tmem_cols;
+  float2* out;
+  int nk, nx, nb, nc;
+  int* err;
+};
+
+struct Tile {
+  int batch, mt, split, kb0, nkb;
+};
+
+__device__ __forceinline__ Tile decode(const TcParams& p, int t) {
+  Tile r;
+  r.split = t % p.nsplit;
+  int rest = t / p.nsplit;
+  r.mt = rest % p.mtiles;
+  r.batch = rest / p.mtiles;
+  r.kb0 = r.split * p.kb_per_split;
+  int left = p.kb_total - r.kb0;
+  r.nkb = left < p.kb_per_split ? left : p.kb_per_split;
+  if (r.nkb < 0) r.nkb = 0;
+  return r;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant__ CUtensorMap ma_lo,
+            const __grid_constant__ CUtensorMap mb_hi, const __grid_constant__ CUtensorMap mb_lo, const TcParams p) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  const int S = p.stages;
+  const uint32_t a_bytes = TC_M * 128;
+  const uint32_t b_bytes = (uint32_t)p.nn * 128;
+  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  unsigned long long* bars = (unsigned long long*)(sm + (size_t)S * stage_bytes);
+  // bars: full[S], empty[S], tfull[2], tempty[2], fin
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 5);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  int* consumed = (int*)(tmem_slot + 2);
+  int* issued = (int*)(tmem_slot + 3);
+  const uint32_t sbase = smem_u32(sm);
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[S + s]); };
+  auto tfull = [&](int a) { return smem_u32(&bars[2 * S + a]); };
+  auto tempty = [&](int a) { return smem_u32(&bars[2 * S + 2 + a]); };
+  const uint32_t fin = smem_u32(&bars[2 * S + 4]);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull(a), 1);
+      mbar_init(tempty(a), 4);
+    }
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    *consumed = 0;
+    *issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), p.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&ma_hi) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&ma_lo) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mb_hi) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&mb_lo) : "memory");
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+      Tile tl = decode(p, t);
+      for (int kb = 0; kb < tl.nkb; ++kb, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = sbase + (uint32_t)s * stage_bytes;
+        mbar_expect_tx(full(s), stage_bytes);
+        const int kc = (tl.kb0 + kb) * TC_KB;
+        tma_load_3d(st, &ma_hi, full(s), kc, tl.mt * TC_M, tl.batch);
+        tma_load_3d(st + a_bytes, &ma_lo, full(s), kc, tl.mt * TC_M, tl.batch);
+        tma_load_3d(st + 2 * a_bytes, &mb_hi, full(s), kc, 0, tl.batch);
+        tma_load_3d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), kc, 0, tl.batch);
+        *(volatile int*)issued = it + 1;
+      }
+    }
+    if (!ok) {
+      atomicExch(p.err, 1);
+      *abort_flag = 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t idesc = idesc_bf16(TC_M, p.nn);
+    int it = 0, local = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++local) {
+      Tile tl = decode(p, t);
+      const int acc = local & 1;
+      const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+      if (!mbar_wait(tempty(acc), aph ^ 1u, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem_base + (uint32_t)(acc * p.nn);
+      for (int kb = 0; kb < tl.nkb; ++kb, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!mbar_wait(full(s), ph, abort_flag)) {
+          ok = false;
+          break;
+        }
+        *(volatile int*)consumed = it + 1;
+        tc_fence_after();
+        const uint32_t st = sbase + (uint32_t)s * stage_bytes;
+#pragma unroll
+        for (int ks = 0; ks < TC_KB / 16; ++ks) {
+          const unsigned long long a_hi = sdesc_sw128(st + ks * 32);
+          const unsigned long long a_lo = sdesc_sw128(st + a_bytes + ks * 32);
+          const unsigned long long b_hi = sdesc_sw128(st + 2 * a_bytes + ks * 32);
+          const unsigned long long b_lo = sdesc_sw128(st + 2 * a_bytes + b_bytes + ks * 32);
+          mma_bf16(d, a_hi, b_hi, idesc, (kb | ks) != 0);
+          mma_bf16(d, a_hi, b_lo, idesc, 1);
+          mma_bf16(d, a_lo, b_hi, idesc, 1);
+        }
+        mma_commit(empty(s));
+      }
+      if (!ok) break;
+      mma_commit(tfull(acc));
+    }
+    if (!ok) {
+      atomicExch(p.err, 1);
+      *abort_flag = 1;
+    }
+    // all issued MMAs retire before the teardown frees TMEM
+    mma_commit(fin);
+    if (!mbar_wait(fin, 0, abort_flag)) {
+      // abort raised elsewhere: still give the last MMAs a bounded grace period
+      const unsigned long long t0 = gtime();
+      while (!mbar_try(fin, 0) && gtime() - t0 < WAIT_NS) {
+      }
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue (128 threads, one TMEM lane each) ----------------
+    const int q = warp & 3;
+    const int row_in_tile = q * 32 + lane;
+    int local = 0;
+    for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++local) {
+      Tile tl = decode(p, t);
+      const int acc = local & 1;
+      const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+      if (!mbar_wait(tfull(acc), aph, abort_flag)) {
+        if (lane == 0) {
+          atomicExch(p.err, 1);
+          *abort_flag = 1;
+        }
+        break;
+      }
+      tc_fence_after();
+      const int row = tl.mt * TC_M + row_in_tile;
+      for (int c16 = 0; c16 < p.nn / 16; ++c16) {
+        float v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * p.nn + c16 * 16), v);
+        if (p.mode == 0) {
+          // phi[k][c][x], x = row
+          if (row < p.nx) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int c = c16 * 8 + i;
+              if (c < p.nc) p.out[((size_t)tl.batch * p.nc + c) * p.nx + row] = make_float2(v[2 * i], v[2 * i + 1]);
+            }
+          }
+        } else {
+          float pv[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) pv[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
+          const int n = row >> 1;
+          if ((lane & 1) == 0 && n < p.nb) {
+            float2* o = p.out + (((size_t)tl.split * p.nk + tl.batch) * p.nb + n) * p.nc;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int c = c16 * 8 + i;
+              if (c < p.nc) o[c] = make_float2(v[2 * i] + pv[2 * i + 1], v[2 * i + 1] - pv[2 * i]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(acc));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // drain TMA copies that were issued but never consumed
+    for (int it = *consumed; it < *issued; ++it) {
+      const unsigned long long t0 = gtime();
+      while (!mbar_try(full(it % S), (uint32_t)(it / S) & 1u) && gtime() - t0 < WAIT_NS) {
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, p.tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation and the FP32 k-transform
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split2(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Bpsi_k[j][q] (hi, lo): j = 2c + s, q = 2n + u; rows j >= 2Nc and q >= 2Nb are zero.
+__global__ void prep_bpsi(const double2* __restrict__ psi, __nv_bfloat16* __restrict__ hi,
+                          __nv_bfloat16* __restrict__ lo, int nk, int nb, int nc, int nn, int kp, int nnmax) {
+  const int k = blockIdx.x;
+  for (int e = threadIdx.x; e < nn * kp; e += blockDim.x) {
+    const int j = e / kp, q = e % kp;
+    const int c = j >> 1, s = j & 1, n = q >> 1, u = q & 1;
+    float val = 0.f;
+    if (c < nc && n < nb) {
+      const double2 ps = psi[((size_t)c * nk + k) * nb + n];
+      // s = 0: Re phi = Ur psi_r - Ui psi_i ; s = 1: Im phi = Ur psi_i + Ui psi_r
+      val = (float)(s == 0 ? (u == 0 ? ps.x : -ps.y) : (u == 0 ? ps.y : ps.x));
+    }
+    __nv_bfloat16 h, l;
+    split2(val, h, l);
+    const size_t o = ((size_t)k * nnmax + j) * kp + q;
+    hi[o] = h;
+    lo[o] = l;
+  }
+}
+
+// 8-point DFT in registers, sign +1: e^{+2 pi i jk/8}, sign -1: e^{-...}
+template <int SIGN>
+__device__ __forceinline__ void dft8(float2* v) {
+  const float r = 0.70710678118654752f;
+  float2 a0 = make_float2(v[0].x + v[4].x, v[0].y + v[4].y), a1 = make_float2(v[0].x - v[4].x, v[0].y - v[4].y);
+  float2 a2 = make_float2(v[2].x + v[6].x, v[2].y + v[6].y), a3 = make_float2(v[2].x - v[6].x, v[2].y - v[6].y);
+  float2 a4 = make_float2(v[1].x + v[5].x, v[1].y + v[5].y), a5 = make_float2(v[1].x - v[5].x, v[1].y - v[5].y);
+  float2 a6 = make_float2(v[3].x + v[7].x, v[3].y + v[7].y), a7 = make_float2(v[3].x - v[7].x, v[3].y - v[7].y);
+  // multiply by w4 = SIGN * i
+  float2 w3 = make_float2(-SIGN * a3.y, SIGN * a3.x), w7 = make_float2(-SIGN * a7.y, SIGN * a7.x);
+  float2 e0 = make_float2(a0.x + a2.x, a0.y + a2.y), e2 = make_float2(a0.x - a2.x, a0.y - a2.y);
+  float2 e1 = make_float2(a1.x + w3.x, a1.y + w3.y), e3 = make_float2(a1.x - w3.x, a1.y - w3.y);
+  float2 o0 = make_float2(a4.x + a6.x, a4.y + a6.y), o2 = make_float2(a4.x - a6.x, a4.y - a6.y);
+  float2 o1 = make_float2(a5.x + w7.x, a5.y + w7.y), o3 = make_float2(a5.x - w7.x, a5.y - w7.y);
+  // twiddles w8^k, w8 = e^{SIGN i pi/4}
+  float2 t1 = make_float2(r * (o1.x - SIGN * o1.y), r * (o1.y + SIGN * o1.x));
+  float2 t2 = make_float2(-SIGN * o2.y, SIGN * o2.x);
+  float2 t3 = make_float2(r * (-o3.x - SIGN * o3.y), r * (-o3.y + SIGN * o3.x));
+  v[0] = make_float2(e0.x + o0.x, e0.y + o0.y);
+  v[4] = make_float2(e0.x - o0.x, e0.y - o0.y);
+  v[1] = make_float2(e1.x + t1.x, e1.y + t1.y);
+  v[5] = make_float2(e1.x - t1.x, e1.y - t1.y);
+  v[2] = make_float2(e2.x + t2.x, e2.y + t2.y);
+  v[6] = make_float2(e2.x - t2.x, e2.y - t2.y);
+  v[3] = make_float2(e3.x + t3.x, e3.y + t3.y);
+  v[7] = make_float2(e3.x - t3.x, e3.y - t3.y);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft_axis_f(float2* S, const float2* tw, int nk, int len, int stride, int ncol) {
+  const int nlines = (nk / len) * ncol;
+  for (int w = threadIdx.x; w < nlines; w += blockDim.x) {
+    const int cc = w % ncol, line = w / ncol;
+    const int inner = line % stride, outer = line / stride;
+    const int base = outer * stride * len + inner;
+    if (len == 1) continue;
+    if (len == 8) {
+      float2 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = S[(size_t)(base + j * stride) * ncol + cc];
+      dft8<SIGN>(v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) S[(size_t)(base + j * stride) * ncol + cc] = v[j];
+      continue;
+    }
+    float2 v[BSE_MAX_NK_AXIS];
+#pragma unroll
+    for (int j = 0; j < BSE_MAX_NK_AXIS; ++j)
+      if (j < len) v[j] = S[(size_t)(base + j * stride) * ncol + cc];
+    for (int qo = 0; qo < len; ++qo) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < BSE_MAX_NK_AXIS; ++j) {
+        if (j < len) {
+          float2 t = tw[(j * qo) % len];
+          if (SIGN < 0) t.y = -t.y;
+          acc.x = fmaf(t.x, v[j].x, fmaf(-t.y, v[j].y, acc.x));
+          acc.y = fmaf(t.x, v[j].y, fmaf(t.y, v[j].x, acc.y));
+        }
+      }
+      S[(size_t)(base + qo * stride) * ncol + cc] = acc;
+    }
+  }
+}
+
+// phi[k][c][x] (FP32) -> (1/Nk) F^- W F^+ over the k mesh -> Bphi_k[2c+s][x] (hi, lo)
+// CTA: XC consecutive x, CG consecutive columns; shared S[k][cl*XC + xl].
+__global__ void __launch_bounds__(256) kconv_tc(const float2* __restrict__ phi, const float* __restrict__ w,
+                                                const double* __restrict__ twiddle, __nv_bfloat16* __restrict__ hi,
+                                                __nv_bfloat16* __restrict__ lo, int nk0, int nk1, int nk2, int nx,
+                                                int nc, int xc, int cg, int nnmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);   // [3][16]
+  float2* S = tw + 48;
+  const int nk = nk0 * nk1 * nk2;
+  const int ncol = xc * cg;
+  const int x0 = blockIdx.x * xc, c0 = blockIdx.y * cg;
+  for (int i = threadIdx.x; i < 48; i += blockDim.x) tw[i] = make_float2((float)twiddle[2 * i], (float)twiddle[2 * i + 1]);
+  for (int e = threadIdx.x; e < nk * ncol; e += blockDim.x) {
+    const int k = e / ncol, cc = e % ncol, cl = cc / xc, xl = cc % xc;
+    const int c = c0 + cl, x = x0 + xl;
+    S[e] = (c < nc && x < nx) ? phi[((size_t)k * nc + c) * nx + x] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  dft_axis_f<+1>(S, tw + 32, nk, nk2, 1, ncol);
+  __syncthreads();
+  dft_axis_f<+1>(S, tw + 16, nk, nk1, nk2, ncol);
+  __syncthreads();
+  dft_axis_f<+1>(S, tw + 0, nk, nk0, nk1 * nk2, ncol);
+  __syncthreads();
+  const float inv = 1.0f / (float)nk;
+  for (int e = threadIdx.x; e < nk * ncol; e += blockDim.x) {
+    const int r = e / ncol, xl = (e % ncol) % xc, x = x0 + xl;
+    const float wv = (x < nx) ? w[(size_t)r * nx + x] * inv : 0.f;
+    S[e].x *= wv;
+    S[e].y *= wv;
+  }
+  __syncthreads();
+  dft_axis_f<-1>(S, tw + 32, nk, nk2, 1, ncol);
+  __syncthreads();
+  dft_axis_f<-1>(S, tw + 16, nk, nk1, nk2, ncol);
+  __syncthreads();
+  dft_axis_f<-1>(S, tw + 0, nk, nk0, nk1 * nk2, ncol);
+  __syncthreads();
+  // rows j = 2c + s, x contiguous
+  for (int e = threadIdx.x; e < nk * cg * 2 * xc; e += blockDim.x) {
+    const int xl = e % xc, rest = e / xc, s = rest % 2, rest2 = rest / 2, cl = rest2 % cg, k = rest2 / cg;
+    const int c = c0 + cl, x = x0 + xl;
+    if (c < nc && x < nx) {
+      const float2 v = S[(size_t)k * ncol + cl * xc + xl];
+      __nv_bfloat16 h, l;
+      split2(s == 0 ? v.x : v.y, h, l);
+      const size_t o = ((size_t)k * nnmax + 2 * c + s) * nx + x;
+      hi[o] = h;
+      lo[o] = l;
+    }
+  }
+}
+
+// out[c][k][n] = sum_split part + E psi - chi psi + short-range out  (FP64)
+__global__ void g2b_final(const float2* __restrict__ part, int nsplit, const double2* __restrict__ psi,
+                          double2* __restrict__ out, const double* __restrict__ e_nk, const double2* __restrict__ chi,
+                          const double2* __restrict__ a_proj, const double2* __restrict__ srcp, int nk, int nb,
+                          int na, int np, int nc) {
+  const size_t nkb = (size_t)nk * nb;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < nkb * nc;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % nc);
+    const size_t kn = idx / nc;
+    const int k = (int)(kn / nb), n = (int)(kn % nb);
+    const int v = c / na, a = c % na;
+    double2 lr = make_double2(0, 0);
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const float2 t = part[((size_t)sp * nkb + kn) * nc + c];
+      lr.x += t.x;
+      lr.y += t.y;
+    }
+    const double2 ps = psi[((size_t)c * nk + k) * nb + n];
+    const double e = e_nk[kn];
+    double2 val = make_double2(lr.x + e * ps.x, lr.y + e * ps.y);
+    for (int b = 0; b < na; ++b) {
+      const double2 ch = chi[a * na + b];
+      const double2 pb = psi[((size_t)(v * na + b) * nk + k) * nb + n];
+      val.x -= ch.x * pb.x - ch.y * pb.y;
+      val.y -= ch.x * pb.y + ch.y * pb.x;
+    }
+    if (np > 0) {
+      const double2* cp = srcp + (size_t)v * na * np + (size_t)a * np;
+      for (int p = 0; p < np; ++p) {
+        const double2 ap = a_proj[(size_t)p * nkb + kn];
+        const double2 qq = cp[p];
+        val.x += ap.x * qq.x + ap.y * qq.y;
+        val.y += ap.x * qq.y - ap.y * qq.x;
+      }
+    }
+    out[((size_t)c * nk + k) * nb + n] = val;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D bf16 map {inner, rows, batch} with row stride `inner_stride` elements and
+// batch stride `batch_stride` elements; box {64, box_rows, 1}, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t batch, uint64_t inner_stride,
+              uint64_t batch_stride, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {inner, rows, batch};
+  cuuint64_t strides[2] = {inner_stride * 2, batch_stride * 2};
+  cuuint32_t box[3] = {(cuuint32_t)TC_KB, box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct TcState {
+  int kp = 0, nnmax = 0, smax = 0, sms = 0;
+  int* err = nullptr;   // device error word
+  CUtensorMap a2_hi, a2_lo, a6_hi, a6_lo;
+};
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+int pick_stages(int nn) {
+  const int stage = 2 * TC_M * 128 + 2 * nn * 128;
+  int s = (SMEM_BUDGET - 1024 - 256) / stage;
+  if (s > 8) s = 8;
+  return s;
+}
+
+bse_status launch_gemm(bse_handle* h, TcState* ts, int mode, const CUtensorMap& a_hi, const CUtensorMap& a_lo,
+                       const CUtensorMap& b_hi, const CUtensorMap& b_lo, TcParams p, int kind) {
+  p.stages = pick_stages(p.nn);
+  if (p.stages < 2) return bse_fail(h, BSE_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * p.nn)) cols <<= 1;
+  p.tmem_cols = cols;
+  p.err = ts->err;
+  const size_t smem = 1024 + (size_t)p.stages * (2 * TC_M * 128 + 2 * p.nn * 128) + 256;
+  cudaFuncSetAttribute(tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = p.ntiles < ts->sms ? p.ntiles : ts->sms;
+  if (grid < 1) return BSE_OK;
+  BSE_PROF(h, kind, tc_gemm<<<grid, TC_THREADS, smem, h->stream>>>(a_hi, a_lo, b_hi, b_lo, p));
+  (void)mode;
+  return bse_cuda_check(h, cudaGetLastError(), "tc_gemm launch");
+}
+
+}  // namespace
+
+bse_status bse_tc_prepare(bse_handle* h) {
+  TcState* ts = new (std::nothrow) TcState();
+  if (!ts) return bse_fail(h, BSE_ERR_OOM, "tc state");
+  h->tmap_host = ts;
+  if (!encode_fn()) return bse_fail(h, BSE_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cudaDeviceGetAttribute(&ts->sms, cudaDevAttrMultiProcessorCount, h->dev);
+  ts->kp = round_up(2 * h->nb, 8);
+  ts->nnmax = round_up(2 * h->na * h->max_vec, 16);
+  // split-K of grid->band: aim for >= 8 work units per SM, >= 8 K blocks per unit
+  const int kbt = (h->nx + TC_KB - 1) / TC_KB;
+  const int units = h->nk * ((2 * h->nb + TC_M - 1) / TC_M);
+  int sp = 1;
+  while (units * sp < 8 * ts->sms && kbt / (sp * 2) >= 8) sp *= 2;
+  ts->smax = sp;
+  const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
+  const size_t nbf = (size_t)h->nk * ts->nnmax * h->nx;
+  if (cudaMalloc((void**)&h->bpsi, 2 * nbp * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc((void**)&h->bphi, 2 * nbf * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc((void**)&h->part, (size_t)ts->smax * h->nk * h->nb * h->na * h->max_vec * sizeof(float2)) !=
+          cudaSuccess ||
+      cudaMalloc((void**)&h->tmap, 256) != cudaSuccess) {
+    cudaGetLastError();
+    return bse_fail(h, BSE_ERR_OOM, "tensor-core scratch");
+  }
+  ts->err = (int*)h->tmap;
+  cudaMemsetAsync(ts->err, 0, 256, h->stream);
+  cudaMemsetAsync(h->bphi, 0, 2 * nbf * sizeof(__nv_bfloat16), h->stream);
+  const int kp = ts->kp;
+  bool ok = make_map(&ts->a2_hi, h->u_hi, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
+            make_map(&ts->a2_lo, h->u_lo, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
+            make_map(&ts->a6_hi, h->ut_hi, h->nx, 2 * h->nb, h->nk, h->nx, (uint64_t)2 * h->nb * h->nx, TC_M) &&
+            make_map(&ts->a6_lo, h->ut_lo, h->nx, 2 * h->nb, h->nk, h->nx, (uint64_t)2 * h->nb * h->nx, TC_M);
+  if (!ok) return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
+  return bse_cuda_check(h, cudaStreamSynchronize(h->stream), "tc prepare");
+}
+
+int bse_tc_kp(const bse_handle* h) { return h->tmap_host ? ((const TcState*)h->tmap_host)->kp : 0; }
+
+void bse_tc_free(bse_handle* h) {
+  delete (TcState*)h->tmap_host;
+  h->tmap_host = nullptr;
+}
+
+bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec) {
+  TcState* ts = (TcState*)h->tmap_host;
+  const int nc = n_vec * h->na;
+  const int nn = round_up(2 * nc, 16);
+  const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
+  __nv_bfloat16* bh = h->bpsi;
+  __nv_bfloat16* bl = h->bpsi + nbp;
+  BSE_PROF(h, BSE_K_PREP, prep_bpsi<<<h->nk, 256, 0, h->stream>>>(psi, bh, bl, h->nk, h->nb, nc, nn, ts->kp, ts->nnmax));
+  CUtensorMap b_hi, b_lo;
+  if (!make_map(&b_hi, bh, ts->kp, nn, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn) ||
+      !make_map(&b_lo, bl, ts->kp, nn, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn))
+    return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
+  TcParams p{};
+  p.mode = 0;
+  p.mtiles = (h->nx + TC_M - 1) / TC_M;
+  p.nsplit = 1;
+  p.kb_total = (ts->kp + TC_KB - 1) / TC_KB;
+  p.kb_per_split = p.kb_total;
+  p.ntiles = h->nk * p.mtiles;
+  p.nn = nn;
+  p.out = (float2*)h->phi;
+  p.nk = h->nk;
+  p.nx = h->nx;
+  p.nb = h->nb;
+  p.nc = nc;
+  return launch_gemm(h, ts, 0, ts->a2_hi, ts->a2_lo, b_hi, b_lo, p, BSE_K_BAND_TO_GRID);
+}
+
+bse_status bse_kconv_bf16(bse_handle* h, int n_vec) {
+  TcState* ts = (TcState*)h->tmap_host;
+  const int nc = n_vec * h->na;
+  const int xc = (h->nx % 16 == 0) ? 16 : 8;
+  int cg = (200 * 1024) / (h->nk * xc * (int)sizeof(float2));
+  if (cg > nc) cg = nc;
+  if (cg < 1) return bse_fail(h, BSE_ERR_UNSUPPORTED, "k mesh too large for the shared-memory k-transform");
+  const size_t smem = (48 + (size_t)h->nk * xc * cg) * sizeof(float2);
+  cudaFuncSetAttribute(kconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t nbf = (size_t)h->nk * ts->nnmax * h->nx;
+  dim3 g((unsigned)((h->nx + xc - 1) / xc), (unsigned)((nc + cg - 1) / cg));
+  BSE_PROF(h, BSE_K_KCONV,
+           kconv_tc<<<g, 256, smem, h->stream>>>((const float2*)h->phi, (const float*)h->w, h->twiddle, h->bphi,
+                                                 h->bphi + nbf, h->nk3[0], h->nk3[1], h->nk3[2], h->nx, nc, xc, cg,
+                                                 ts->nnmax));
+  return bse_cuda_check(h, cudaGetLastError(), "kconv_tc launch");
+}
+
+bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec) {
+  TcState* ts = (TcState*)h->tmap_host;
+  const int nc = n_vec * h->na;
+  const int nn = round_up(2 * nc, 16);
+  const size_t nbf = (size_t)h->nk * ts->nnmax * h->nx;
+  CUtensorMap b_hi, b_lo;
+  if (!make_map(&b_hi, h->bphi, h->nx, nn, h->nk, h->nx, (uint64_t)ts->nnmax * h->nx, nn) ||
+      !make_map(&b_lo, h->bphi + nbf, h->nx, nn, h->nk, h->nx, (uint64_t)ts->nnmax * h->nx, nn))
+    return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
+  TcParams p{};
+  p.mode = 1;
+  p.mtiles = (2 * h->nb + TC_M - 1) / TC_M;
+  p.kb_total = (h->nx + TC_KB - 1) / TC_KB;
+  p.nsplit = ts->smax < p.kb_total ? ts->smax : p.kb_total;
+  p.kb_per_split = (p.kb_total + p.nsplit - 1) / p.nsplit;
+  p.nsplit = (p.kb_total + p.kb_per_split - 1) / p.kb_per_split;   // no empty split
+  p.ntiles = h->nk * p.mtiles * p.nsplit;
+  p.nn = nn;
+  p.out = (float2*)h->part;
+  p.nk = h->nk;
+  p.nx = h->nx;
+  p.nb = h->nb;
+  p.nc = nc;
+  bse_status s = launch_gemm(h, ts, 1, ts->a6_hi, ts->a6_lo, b_hi, b_lo, p, BSE_K_GRID_TO_BAND);
+  if (s != BSE_OK) return s;
+  const size_t total = (size_t)h->nk * h->nb * nc;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  BSE_PROF(h, BSE_K_PREP,
+           g2b_final<<<blocks, 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
+                                                    h->a_proj, h->sr_cp, h->nk, h->nb, h->na, h->np, nc));
+  return bse_cuda_check(h, cudaGetLastError(), "g2b_final launch");
+}
+
+bse_status bse_tc_status(bse_handle* h) {
+  if (h->prec != BSE_PREC_SPLIT_BF16 || !h->tmap_host) return BSE_OK;
+  TcState* ts = (TcState*)h->tmap_host;
+  int e = 0;
+  if (cudaMemcpy(&e, ts->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bse_cuda_check(h, cudaGetLastError(), "tc status");
+  if (e) return bse_fail(h, BSE_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+  return BSE_OK;
+}
