@@ -72,6 +72,7 @@ struct bse_handle {
   void* phi = nullptr;        // [Nk][Nx][Nc] complex (double2 for FP64, float2 otherwise)
   double2* sr_c = nullptr;    // [max_vec][Na*Np]
   double2* sr_cp = nullptr;   // [max_vec][Na*Np]
+  double2* sr_part = nullptr; // [ceil(Nk*Nb/64)][max_vec*Na][Np] split-K partial projections
   __nv_bfloat16* bpsi = nullptr;    // SPLIT_BF16: [Nk][2][Nrow][2Nb] B operand of band->grid
   __nv_bfloat16* bphi = nullptr;    // SPLIT_BF16: [Nk][2][Nrow][Nx]  B operand of grid->band
   float* part = nullptr;            // SPLIT_BF16: split-K partial tiles

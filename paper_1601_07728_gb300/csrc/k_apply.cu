@@ -75,6 +75,34 @@ __global__ void __launch_bounds__(256) b2g_simt(const typename Cx<T>::type* __re
 // F^{+/-} are 3-D DFTs over the (nk0, nk1, nk2) mesh, computed axis by axis in
 // shared memory with explicit sums (nk_d <= 16).
 // ---------------------------------------------------------------------------
+// radix-2 8-point DFT in registers: v_q <- sum_j e^{SIGN 2 pi i j q / 8} v_j
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft8_simt(typename Cx<T>::type* v) {
+  typedef typename Cx<T>::type C;
+  const T r = (T)0.70710678118654752440;
+  auto add = [](C a, C b) { C o; o.x = a.x + b.x; o.y = a.y + b.y; return o; };
+  auto sub = [](C a, C b) { C o; o.x = a.x - b.x; o.y = a.y - b.y; return o; };
+  auto mi = [](C a) { C o; o.x = -SIGN * a.y; o.y = SIGN * a.x; return o; };   // times SIGN*i
+  C a0 = add(v[0], v[4]), a1 = sub(v[0], v[4]), a2 = add(v[2], v[6]), a3 = sub(v[2], v[6]);
+  C a4 = add(v[1], v[5]), a5 = sub(v[1], v[5]), a6 = add(v[3], v[7]), a7 = sub(v[3], v[7]);
+  C e0 = add(a0, a2), e2 = sub(a0, a2), e1 = add(a1, mi(a3)), e3 = sub(a1, mi(a3));
+  C o0 = add(a4, a6), o2 = sub(a4, a6), o1 = add(a5, mi(a7)), o3 = sub(a5, mi(a7));
+  C t1, t3;
+  t1.x = r * (o1.x - SIGN * o1.y);
+  t1.y = r * (o1.y + SIGN * o1.x);
+  C t2 = mi(o2);
+  t3.x = r * (-o3.x - SIGN * o3.y);
+  t3.y = r * (-o3.y + SIGN * o3.x);
+  v[0] = add(e0, o0);
+  v[4] = sub(e0, o0);
+  v[1] = add(e1, t1);
+  v[5] = sub(e1, t1);
+  v[2] = add(e2, t2);
+  v[6] = sub(e2, t2);
+  v[3] = add(e3, t3);
+  v[7] = sub(e3, t3);
+}
+
 template <typename T, int SIGN>
 __device__ __forceinline__ void dft_axis(typename Cx<T>::type* S, const typename Cx<T>::type* tw, int nk,
                                          int len, int stride, int CCn) {
@@ -85,6 +113,16 @@ __device__ __forceinline__ void dft_axis(typename Cx<T>::type* S, const typename
     // line -> base k index: split line into (outer, inner) around the axis
     int inner = line % stride, outer = line / stride;
     int base = outer * stride * len + inner;
+    if (len == 1) continue;
+    if (len == 8) {
+      C v8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v8[j] = S[(size_t)(base + j * stride) * CCn + cc];
+      dft8_simt<T, SIGN>(v8);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) S[(size_t)(base + j * stride) * CCn + cc] = v8[j];
+      continue;
+    }
     C v[BSE_MAX_NK_AXIS];
 #pragma unroll
     for (int j = 0; j < BSE_MAX_NK_AXIS; ++j)
@@ -283,6 +321,74 @@ __global__ void __launch_bounds__(256) sr_couple_kernel(const double2* __restric
   }
 }
 
+// Split-K projection onto the local basis: block b sums kn in [b*SRK, (b+1)*SRK)
+// for up to SRC columns and all Np functions; part[b][c][p].
+constexpr int SRK = 64, SRC = 16;
+__global__ void __launch_bounds__(256) sr_in_partial(const double2* __restrict__ a_proj,
+                                                     const double2* __restrict__ psi,
+                                                     double2* __restrict__ part, int nkb, int np, int nc) {
+  extern __shared__ __align__(16) unsigned char sr_smem[];
+  double2* As = reinterpret_cast<double2*>(sr_smem);   // [np][SRK + 1]
+  double2* Ps = As + (size_t)np * (SRK + 1);            // [SRC][SRK + 1]
+  const int b = blockIdx.x, c0 = blockIdx.y * SRC;
+  const int ncc = nc - c0 < SRC ? nc - c0 : SRC;
+  const int k0 = b * SRK;
+  for (int e = threadIdx.x; e < np * SRK; e += blockDim.x) {
+    const int p = e / SRK, i = e % SRK;
+    As[p * (SRK + 1) + i] = (k0 + i < nkb) ? a_proj[(size_t)p * nkb + k0 + i] : make_double2(0, 0);
+  }
+  for (int e = threadIdx.x; e < ncc * SRK; e += blockDim.x) {
+    const int c = e / SRK, i = e % SRK;
+    Ps[c * (SRK + 1) + i] = (k0 + i < nkb) ? psi[(size_t)(c0 + c) * nkb + k0 + i] : make_double2(0, 0);
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < ncc * np; o += blockDim.x) {
+    const int c = o / np, p = o % np;
+    double re = 0, im = 0;
+#pragma unroll 8
+    for (int i = 0; i < SRK; ++i) {
+      const double2 a = As[p * (SRK + 1) + i], q = Ps[c * (SRK + 1) + i];
+      re += a.x * q.x - a.y * q.y;
+      im += a.x * q.y + a.y * q.x;
+    }
+    part[((size_t)b * nc + c0 + c) * np + p] = make_double2(re, im);
+  }
+}
+
+// c[o] = sum_b part[b][o]  (fixed order), o over (c, p)
+__global__ void sr_reduce(const double2* __restrict__ part, double2* __restrict__ src, int nblk, int nout) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double re = 0, im = 0;
+  for (int b = 0; b < nblk; ++b) {
+    const double2 t = part[(size_t)b * nout + o];
+    re += t.x;
+    im += t.y;
+  }
+  src[o] = make_double2(re, im);
+}
+
+// c'[v][i] = sum_j M[i][j] c[v][j]: one warp per row i
+__global__ void __launch_bounds__(256) sr_couple_warp(const double2* __restrict__ m, const double2* __restrict__ src,
+                                                      double2* __restrict__ srcp, int dimm) {
+  const int v = blockIdx.y;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= dimm) return;
+  const double2* mr = m + (size_t)i * dimm;
+  const double2* cv = src + (size_t)v * dimm;
+  double re = 0, im = 0;
+  for (int j = lane; j < dimm; j += 32) {
+    const double2 a = mr[j], q = cv[j];
+    re += a.x * q.x - a.y * q.y;
+    im += a.x * q.y + a.y * q.x;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
+  if (lane == 0) srcp[(size_t)v * dimm + i] = make_double2(re, im);
+}
+
 template <typename T>
 bse_status apply_simt(bse_handle* h, const double2* psi, double2* hpsi, int n_vec) {
   typedef typename Cx<T>::type C;
@@ -322,9 +428,22 @@ bse_status bse_sr_terms(bse_handle* h, const double2* psi, int n_vec) {
   if (h->np <= 0) return BSE_OK;
   cudaStream_t st = h->stream;
   const int nc = n_vec * h->na;
-  dim3 g((unsigned)h->np, (unsigned)nc);
-  BSE_PROF(h, BSE_K_SR_IN, sr_in_kernel<<<g, 256, 0, st>>>(h->a_proj, psi, h->sr_c, h->nk * h->nb, h->np));
-  BSE_PROF(h, BSE_K_SR_COUPLE, sr_couple_kernel<<<n_vec, 256, 0, st>>>(h->m_sr, h->sr_c, h->sr_cp, h->na * h->np));
+  const int nkb = h->nk * h->nb;
+  if (h->sr_part) {
+    const int nblk = (nkb + SRK - 1) / SRK;
+    dim3 g((unsigned)nblk, (unsigned)((nc + SRC - 1) / SRC));
+    const size_t smem = (size_t)(h->np + SRC) * (SRK + 1) * sizeof(double2);
+    cudaFuncSetAttribute(sr_in_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    BSE_PROF(h, BSE_K_SR_IN, sr_in_partial<<<g, 256, smem, st>>>(h->a_proj, psi, h->sr_part, nkb, h->np, nc));
+    const int nout = nc * h->np;
+    BSE_PROF(h, BSE_K_SR_IN, sr_reduce<<<(nout + 255) / 256, 256, 0, st>>>(h->sr_part, h->sr_c, nblk, nout));
+  } else {
+    dim3 g((unsigned)h->np, (unsigned)nc);
+    BSE_PROF(h, BSE_K_SR_IN, sr_in_kernel<<<g, 256, 0, st>>>(h->a_proj, psi, h->sr_c, nkb, h->np));
+  }
+  const int dimm = h->na * h->np;
+  dim3 gc((unsigned)((dimm + 7) / 8), (unsigned)n_vec);
+  BSE_PROF(h, BSE_K_SR_COUPLE, sr_couple_warp<<<gc, 256, 0, st>>>(h->m_sr, h->sr_c, h->sr_cp, dimm));
   return bse_cuda_check(h, cudaGetLastError(), "short-range kernels");
 }
 

@@ -175,6 +175,8 @@ bse_status bse_setup_device(bse_handle* h, const bse_system_desc* d) {
     TRY(bse_cuda_check(h, cudaMemcpyAsync(h->m_sr, d->m_sr, (size_t)h->na * h->np * h->na * h->np * sizeof(double2), cudaMemcpyDefault, st), "copy m_sr"));
     TRY(dev_alloc(h, &h->sr_c, (size_t)h->max_vec * h->na * h->np * sizeof(double2), "sr_c"));
     TRY(dev_alloc(h, &h->sr_cp, (size_t)h->max_vec * h->na * h->np * sizeof(double2), "sr_cp"));
+    const size_t nblk = (nkb + 63) / 64;
+    TRY(dev_alloc(h, &h->sr_part, nblk * h->max_vec * h->na * h->np * sizeof(double2), "sr_part"));
   }
 
   // twiddles e^{+2 pi i j / n} per axis (host libm, FP64)

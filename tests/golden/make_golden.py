@@ -32,5 +32,20 @@ def main():
                 f.write("%d %.17e %.17e\n" % (i, ai, bb[i]))
 
 
-if __name__ == "__main__":
+if __name__ == "__main__" and len(sys.argv) == 1:
     main()
+
+
+def l23_spectrum(n_steps=200):
+    """Oracle Haydock run (plain Lanczos, like the benchmark) on the full
+    L2,3-edge workload; stores a_i, b_i and the spectrum on the 2000-point grid."""
+    s = S.make_system("l23_multiplet")
+    b = S.make_start_vectors(s, 1)[0]
+    a, bb, nd, brk = O.haydock(lambda v: O.apply_h(s, v), b, n_steps)
+    sig = O.cf_spectrum(a, bb, S.omega_grid(), 0.5)
+    np.savez_compressed(os.path.join(HERE, "l23_multiplet_haydock200.npz"), a=a, b=bb, sigma=sig,
+                        omega=S.omega_grid(), steps=nd)
+
+
+if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "l23":
+    l23_spectrum()
