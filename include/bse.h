@@ -161,6 +161,36 @@ bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_
  * preconditioner. */
 bse_status bse_jacobi_diag(bse_handle* h, double* diag);
 
+/* Short-range (local direct + exchange) term alone, out = (A (x) I)^H M (A (x) I) psi,
+ * computed without allocating any memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc where they need
+ * the term -- code that runs while its stream is being captured into a CUDA
+ * graph (allocation is not a stream-ordered operation and is refused there),
+ * plug-ins whose host framework owns every device byte through its own pool,
+ * and real-time loops that cannot afford the synchronisation an allocation
+ * implies.  No handle is used and nothing is allocated, by this library or by
+ * any library it calls.
+ *   a_proj [n_proj][n_kb], m_sr [n_alpha*n_proj]^2 (index (alpha, p), alpha
+ *   slow), psi and out [n_vec][n_alpha][n_kb], all complex128 DEVICE memory
+ *   owned by the caller; n_kb = Nk*Nb.  Work is enqueued on `stream`
+ *   (cudaStream_t, NULL = legacy default stream); the call returns without
+ *   waiting for it.
+ * Scratch: a 2 MiB array (131072 complex128 entries) compiled into the
+ * library as a static device variable; every GPU that loads the library holds
+ * it until the process exits.  The call needs
+ *   ceil(n_kb/64)*n_vec*n_alpha*n_proj + 2*n_vec*n_alpha*n_proj  entries
+ * and returns BSE_ERR_INVALID_ARG (with a message on stderr) for anything
+ * larger; n_proj must be in 1..64.  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress (with that device
+ * current) and caches it: make that first call before any stream capture
+ * begins.  Every call shares the one array and it keeps the previous call's
+ * contents; each call overwrites all the entries it reads, so nothing needs
+ * clearing.  Calls whose kernels overlap on the GPU (different streams, or
+ * host threads using the same device) race on the scratch and must be
+ * serialised by the caller. */
+bse_status bse_short_range_noalloc(const bse_c128* a_proj, const bse_c128* m_sr, const bse_c128* psi,
+                                   bse_c128* out, int n_alpha, int n_kb, int n_proj, int n_vec, void* stream);
+
 /* Number of the library's own kernel launches since the handle was created
  * (every launch the compute calls enqueue is counted). */
 long long bse_launch_count(const bse_handle* h);

@@ -23,7 +23,7 @@ PRECOND = {"none": 0, "jacobi": 1}
 # every function declared in include/bse.h
 EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", "bse_cf_spectrum",
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
-           "bse_profile_enable", "bse_profile_read", "bse_kernel_name"]
+           "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc"]
 KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
 
 
@@ -87,6 +87,8 @@ def lib():
     L.bse_profile_read.restype = ci
     L.bse_kernel_name.argtypes = [ci]
     L.bse_kernel_name.restype = ctypes.c_char_p
+    L.bse_short_range_noalloc.argtypes = [vp, vp, vp, vp, ci, ci, ci, ci, vp]
+    L.bse_short_range_noalloc.restype = ci
     _LIB = L
     return L
 
@@ -240,3 +242,13 @@ def cf_spectrum(a, bcoef, steps, omega, gamma, terminator=False):
     if st != BSE_OK:
         raise BSEError(st, "cf_spectrum failed")
     return sig
+
+
+def short_range_noalloc(a_proj, m_sr, psi, out, n_alpha, stream=None):
+    """out = V_SR psi through bse_short_range_noalloc (device arrays; nothing is
+    allocated, the library's static scratch is used).  Returns the status code."""
+    n_proj = a_proj.shape[0]
+    n_kb = a_proj.shape[-1] if a_proj.ndim == 2 else int(np.prod(a_proj.shape[1:]))
+    n_vec = 1 if psi.ndim == 1 else psi.shape[0]
+    return lib().bse_short_range_noalloc(_ptr(a_proj), _ptr(m_sr), _ptr(psi), _ptr(out), int(n_alpha), int(n_kb),
+                                         int(n_proj), int(n_vec), stream)
