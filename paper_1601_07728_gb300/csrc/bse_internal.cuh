@@ -131,6 +131,9 @@ bse_status bse_tc_prepare(bse_handle* h);
 bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec);
 bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec);
 bse_status bse_kconv_bf16(bse_handle* h, int n_vec);
+// k-transform x W (k_kconv.cu): in place on phi[k][c][x], or into bf16 hi/lo planes
+bse_status bse_kconv_inplace(bse_handle* h, int n_vec);
+bse_status bse_kconv_split(bse_handle* h, int n_vec, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax);
 bse_status bse_tc_status(bse_handle* h);   // device error word of the tensor-core pipeline
 void bse_tc_free(bse_handle* h);
 

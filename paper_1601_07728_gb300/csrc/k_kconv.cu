@@ -1,0 +1,374 @@
+// k -> R Fourier sum, multiplication by W(x, R) and R -> k sum of Algorithm 1
+// (Sec. 3.2.1, lines 3-5), applied to every column (x, c) of phi[k][c][x]:
+//     phi'(x, k) = (1/Nk) sum_R e^{-ik.R} W(x, R) sum_k' e^{+ik'.R} phi(x, k').
+// The 3-D transform over the k mesh is done axis by axis.
+//
+// kconv_cubic<T, N, BF16>: cubic mesh N x N x N (N <= 8).  One CTA owns one
+// column c and 16 consecutive x; thread (g, xl) works on whole pencils, so each
+// 1-D transform runs in registers.  The first forward pass is fused into the
+// global load, the multiplication by W sits between the forward and inverse
+// transforms along the last axis, and the last inverse pass is fused into the
+// store (either complex T in place, or the bf16 hi/lo planes the tensor-core
+// grid->band GEMM reads).
+// kconv_generic<T, BF16>: any mesh with axes <= 16, one pass per axis in
+// shared memory with explicit sums.
+#include "bse_internal.cuh"
+
+namespace {
+
+template <typename T> struct CT;
+template <> struct CT<float> { typedef float2 t; };
+template <> struct CT<double> { typedef double2 t; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C o; o.x = a.x + b.x; o.y = a.y + b.y; return o; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C o; o.x = a.x - b.x; o.y = a.y - b.y; return o; }
+// a * (SIGN i)
+template <int SIGN, typename C> __device__ __forceinline__ C cmuli(C a) { C o; o.x = -SIGN * a.y; o.y = SIGN * a.x; return o; }
+// a * b
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  C o;
+  o.x = a.x * b.x - a.y * b.y;
+  o.y = a.x * b.y + a.y * b.x;
+  return o;
+}
+
+// v_q <- sum_j e^{SIGN 2 pi i j q / N} v_j ; tw[j] = e^{+2 pi i j / N}
+template <typename T, int N, int SIGN>
+__device__ __forceinline__ void dftN(typename CT<T>::t* v, const typename CT<T>::t* tw) {
+  typedef typename CT<T>::t C;
+  if constexpr (N == 1) {
+    return;
+  } else if constexpr (N == 2) {
+    C a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
+    v[0] = a;
+    v[1] = b;
+  } else if constexpr (N == 4) {
+    C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]), a2 = cadd(v[1], v[3]), a3 = cmuli<SIGN>(csub(v[1], v[3]));
+    v[0] = cadd(a0, a2);
+    v[2] = csub(a0, a2);
+    v[1] = cadd(a1, a3);
+    v[3] = csub(a1, a3);
+  } else if constexpr (N == 8) {
+    const T r = (T)0.70710678118654752440;
+    C a0 = cadd(v[0], v[4]), a1 = csub(v[0], v[4]), a2 = cadd(v[2], v[6]), a3 = csub(v[2], v[6]);
+    C a4 = cadd(v[1], v[5]), a5 = csub(v[1], v[5]), a6 = cadd(v[3], v[7]), a7 = csub(v[3], v[7]);
+    C e0 = cadd(a0, a2), e2 = csub(a0, a2), e1 = cadd(a1, cmuli<SIGN>(a3)), e3 = csub(a1, cmuli<SIGN>(a3));
+    C o0 = cadd(a4, a6), o2 = csub(a4, a6), o1 = cadd(a5, cmuli<SIGN>(a7)), o3 = csub(a5, cmuli<SIGN>(a7));
+    C t1, t3;
+    t1.x = r * (o1.x - SIGN * o1.y);
+    t1.y = r * (o1.y + SIGN * o1.x);
+    C t2 = cmuli<SIGN>(o2);
+    t3.x = r * (-o3.x - SIGN * o3.y);
+    t3.y = r * (-o3.y + SIGN * o3.x);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, t1);
+    v[5] = csub(e1, t1);
+    v[2] = cadd(e2, t2);
+    v[6] = csub(e2, t2);
+    v[3] = cadd(e3, t3);
+    v[7] = csub(e3, t3);
+  } else {
+    C out[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      C acc;
+      acc.x = 0;
+      acc.y = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        C t = tw[(j * q) % N];
+        if (SIGN < 0) t.y = -t.y;
+        C p = cmulc(t, v[j]);
+        acc.x += p.x;
+        acc.y += p.y;
+      }
+      out[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = out[q];
+  }
+}
+
+__device__ __forceinline__ void split_bf(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+constexpr int XC = 16;   // consecutive x per CTA
+
+template <typename T, int N, bool BF16>
+__global__ void __launch_bounds__(256) kconv_cubic(typename CT<T>::t* __restrict__ phi, const T* __restrict__ w,
+                                                   const double* __restrict__ twiddle, __nv_bfloat16* __restrict__ hi,
+                                                   __nv_bfloat16* __restrict__ lo, int nx, int nc, int nnmax) {
+  typedef typename CT<T>::t C;
+  constexpr int NK = N * N * N, NP = N * N;           // points, pencils per axis
+  constexpr int PPT = (NP + 15) / 16;                  // pencils per thread
+  extern __shared__ __align__(16) unsigned char kc_smem[];
+  C* S = reinterpret_cast<C*>(kc_smem);               // [NK][XC]
+  const int xl = threadIdx.x & (XC - 1), g = threadIdx.x >> 4;
+  const int c = blockIdx.y, x0 = blockIdx.x * XC, x = x0 + xl;
+  const bool xin = x < nx;
+  C tw[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    tw[j].x = (T)twiddle[2 * j];   // axis-0 twiddles (cubic mesh: every axis the same)
+    tw[j].y = (T)twiddle[2 * j + 1];
+  }
+  const size_t colstride = (size_t)nc * nx;   // distance between consecutive k in phi
+  C* base = phi + (size_t)c * nx + x;
+  // pass A: global load + forward transform along axis 2 (k = (m0 N + m1) N + m2)
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + 16 * i;
+    if (p < NP) {
+      C v[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        if (xin) {
+          v[j] = base[(size_t)(p * N + j) * colstride];
+        } else {
+          v[j].x = 0;
+          v[j].y = 0;
+        }
+      }
+      dftN<T, N, +1>(v, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[(p * N + j) * XC + xl] = v[j];
+    }
+  }
+  __syncthreads();
+  // pass B: forward along axis 1; pencil p = (m0, m2): k = m0 N^2 + j N + m2
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + 16 * i;
+    if (p < NP) {
+      const int kb = (p / N) * NP + (p % N);
+      C v[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = S[(kb + j * N) * XC + xl];
+      dftN<T, N, +1>(v, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[(kb + j * N) * XC + xl] = v[j];
+    }
+  }
+  __syncthreads();
+  // pass C: forward along axis 0, times W(x, R)/Nk, inverse along axis 0; p = (m1, m2): k = j N^2 + p
+  const T inv = (T)1 / (T)NK;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + 16 * i;
+    if (p < NP) {
+      C v[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = S[(j * NP + p) * XC + xl];
+      dftN<T, N, +1>(v, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const T wv = xin ? w[(size_t)(j * NP + p) * nx + x] * inv : (T)0;
+        v[j].x *= wv;
+        v[j].y *= wv;
+      }
+      dftN<T, N, -1>(v, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[(j * NP + p) * XC + xl] = v[j];
+    }
+  }
+  __syncthreads();
+  // pass D: inverse along axis 1
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + 16 * i;
+    if (p < NP) {
+      const int kb = (p / N) * NP + (p % N);
+      C v[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = S[(kb + j * N) * XC + xl];
+      dftN<T, N, -1>(v, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[(kb + j * N) * XC + xl] = v[j];
+    }
+  }
+  __syncthreads();
+  // pass E: inverse along axis 2 + store
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + 16 * i;
+    if (p < NP) {
+      C v[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = S[(p * N + j) * XC + xl];
+      dftN<T, N, -1>(v, tw);
+      if (xin) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int k = p * N + j;
+          if constexpr (BF16) {
+            const size_t o = ((size_t)k * nnmax + 2 * c) * nx + x;
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf((float)v[j].x, h0, l0);
+            split_bf((float)v[j].y, h1, l1);
+            hi[o] = h0;
+            lo[o] = l0;
+            hi[o + nx] = h1;
+            lo[o + nx] = l1;
+          } else {
+            base[(size_t)k * colstride] = v[j];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Generic mesh: one shared-memory pass per axis with explicit sums; CTA owns
+// XC consecutive x of one column c.  S[k][xl].
+template <typename T, int SIGN>
+__device__ void axis_pass(typename CT<T>::t* S, const typename CT<T>::t* tw, int nk, int len, int stride) {
+  typedef typename CT<T>::t C;
+  const int nlines = (nk / len) * XC;
+  for (int wv = threadIdx.x; wv < nlines; wv += blockDim.x) {
+    const int xl = wv & (XC - 1), line = wv / XC;
+    const int inner = line % stride, outer = line / stride;
+    const int b = outer * stride * len + inner;
+    C v[BSE_MAX_NK_AXIS];
+#pragma unroll
+    for (int j = 0; j < BSE_MAX_NK_AXIS; ++j)
+      if (j < len) v[j] = S[(b + j * stride) * XC + xl];
+    for (int q = 0; q < len; ++q) {
+      C acc;
+      acc.x = 0;
+      acc.y = 0;
+#pragma unroll
+      for (int j = 0; j < BSE_MAX_NK_AXIS; ++j) {
+        if (j < len) {
+          C t = tw[(j * q) % len];
+          if (SIGN < 0) t.y = -t.y;
+          C p = cmulc(t, v[j]);
+          acc.x += p.x;
+          acc.y += p.y;
+        }
+      }
+      S[(b + q * stride) * XC + xl] = acc;
+    }
+  }
+}
+
+template <typename T, bool BF16>
+__global__ void __launch_bounds__(256) kconv_generic(typename CT<T>::t* __restrict__ phi, const T* __restrict__ w,
+                                                     const double* __restrict__ twiddle,
+                                                     __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                                     int nk0, int nk1, int nk2, int nx, int nc, int nnmax) {
+  typedef typename CT<T>::t C;
+  extern __shared__ __align__(16) unsigned char kg_smem[];
+  C* tw = reinterpret_cast<C*>(kg_smem);   // [3][16]
+  C* S = tw + 48;                          // [Nk][XC]
+  const int nk = nk0 * nk1 * nk2;
+  const int c = blockIdx.y, x0 = blockIdx.x * XC;
+  for (int i = threadIdx.x; i < 48; i += blockDim.x) {
+    tw[i].x = (T)twiddle[2 * i];
+    tw[i].y = (T)twiddle[2 * i + 1];
+  }
+  const size_t colstride = (size_t)nc * nx;
+  for (int e = threadIdx.x; e < nk * XC; e += blockDim.x) {
+    const int k = e / XC, xl = e % XC, x = x0 + xl;
+    C z;
+    z.x = 0;
+    z.y = 0;
+    S[e] = x < nx ? phi[(size_t)k * colstride + (size_t)c * nx + x] : z;
+  }
+  __syncthreads();
+  axis_pass<T, +1>(S, tw + 32, nk, nk2, 1);
+  __syncthreads();
+  axis_pass<T, +1>(S, tw + 16, nk, nk1, nk2);
+  __syncthreads();
+  axis_pass<T, +1>(S, tw, nk, nk0, nk1 * nk2);
+  __syncthreads();
+  const T inv = (T)1 / (T)nk;
+  for (int e = threadIdx.x; e < nk * XC; e += blockDim.x) {
+    const int r = e / XC, x = x0 + e % XC;
+    const T wv = x < nx ? w[(size_t)r * nx + x] * inv : (T)0;
+    S[e].x *= wv;
+    S[e].y *= wv;
+  }
+  __syncthreads();
+  axis_pass<T, -1>(S, tw + 32, nk, nk2, 1);
+  __syncthreads();
+  axis_pass<T, -1>(S, tw + 16, nk, nk1, nk2);
+  __syncthreads();
+  axis_pass<T, -1>(S, tw, nk, nk0, nk1 * nk2);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nk * XC; e += blockDim.x) {
+    const int k = e / XC, x = x0 + e % XC;
+    if (x >= nx) continue;
+    if constexpr (BF16) {
+      const size_t o = ((size_t)k * nnmax + 2 * c) * nx + x;
+      __nv_bfloat16 h0, l0, h1, l1;
+      split_bf((float)S[e].x, h0, l0);
+      split_bf((float)S[e].y, h1, l1);
+      hi[o] = h0;
+      lo[o] = l0;
+      hi[o + nx] = h1;
+      lo[o + nx] = l1;
+    } else {
+      phi[(size_t)k * colstride + (size_t)c * nx + x] = S[e];
+    }
+  }
+}
+
+template <typename T, int N, bool BF16>
+void launch_cubic(bse_handle* h, dim3 g, typename CT<T>::t* phi, const T* w, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                  int nc, int nnmax) {
+  const size_t smem = (size_t)N * N * N * XC * sizeof(typename CT<T>::t);
+  cudaFuncSetAttribute(kconv_cubic<T, N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  BSE_PROF(h, BSE_K_KCONV,
+           kconv_cubic<T, N, BF16><<<g, 256, smem, h->stream>>>(phi, w, h->twiddle, hi, lo, h->nx, nc, nnmax));
+}
+
+template <typename T, bool BF16>
+bse_status launch(bse_handle* h, int nc, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax) {
+  typedef typename CT<T>::t C;
+  C* phi = (C*)h->phi;
+  const T* w = (const T*)h->w;
+  const dim3 g((unsigned)((h->nx + XC - 1) / XC), (unsigned)nc);
+  const int n = h->nk3[0];
+  if (h->nk3[1] == n && h->nk3[2] == n && n <= 8) {
+#define KCUBIC(NN)                                                  \
+  case NN:                                                          \
+    launch_cubic<T, NN, BF16>(h, g, phi, w, hi, lo, nc, nnmax);     \
+    break;
+    switch (n) {
+      KCUBIC(1)
+      KCUBIC(2)
+      KCUBIC(3)
+      KCUBIC(4)
+      KCUBIC(5)
+      KCUBIC(6)
+      KCUBIC(7)
+      KCUBIC(8)
+    }
+#undef KCUBIC
+  } else {
+    const size_t smem = (48 + (size_t)h->nk * XC) * sizeof(C);
+    if (smem > 220 * 1024) return bse_fail(h, BSE_ERR_UNSUPPORTED, "k mesh too large for the shared-memory transform");
+    cudaFuncSetAttribute(kconv_generic<T, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    BSE_PROF(h, BSE_K_KCONV,
+             kconv_generic<T, BF16><<<g, 256, smem, h->stream>>>(phi, w, h->twiddle, hi, lo, h->nk3[0], h->nk3[1],
+                                                                 h->nk3[2], h->nx, nc, nnmax));
+  }
+  return bse_cuda_check(h, cudaGetLastError(), "k-transform launch");
+}
+
+}  // namespace
+
+// phi[k][c][x] in place (FP64 / FP32 forms)
+bse_status bse_kconv_inplace(bse_handle* h, int n_vec) {
+  const int nc = n_vec * h->na;
+  if (h->prec == BSE_PREC_FP64) return launch<double, false>(h, nc, nullptr, nullptr, 0);
+  return launch<float, false>(h, nc, nullptr, nullptr, 0);
+}
+
+// phi[k][c][x] (FP32) -> bf16 hi/lo planes [k][2c+s][x] with row stride nnmax
+bse_status bse_kconv_split(bse_handle* h, int n_vec, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax) {
+  return launch<float, true>(h, n_vec * h->na, hi, lo, nnmax);
+}

@@ -394,125 +394,6 @@ __global__ void prep_bpsi(const double2* __restrict__ psi, __nv_bfloat16* __rest
   }
 }
 
-// 8-point DFT in registers, sign +1: e^{+2 pi i jk/8}, sign -1: e^{-...}
-template <int SIGN>
-__device__ __forceinline__ void dft8(float2* v) {
-  const float r = 0.70710678118654752f;
-  float2 a0 = make_float2(v[0].x + v[4].x, v[0].y + v[4].y), a1 = make_float2(v[0].x - v[4].x, v[0].y - v[4].y);
-  float2 a2 = make_float2(v[2].x + v[6].x, v[2].y + v[6].y), a3 = make_float2(v[2].x - v[6].x, v[2].y - v[6].y);
-  float2 a4 = make_float2(v[1].x + v[5].x, v[1].y + v[5].y), a5 = make_float2(v[1].x - v[5].x, v[1].y - v[5].y);
-  float2 a6 = make_float2(v[3].x + v[7].x, v[3].y + v[7].y), a7 = make_float2(v[3].x - v[7].x, v[3].y - v[7].y);
-  // multiply by w4 = SIGN * i
-  float2 w3 = make_float2(-SIGN * a3.y, SIGN * a3.x), w7 = make_float2(-SIGN * a7.y, SIGN * a7.x);
-  float2 e0 = make_float2(a0.x + a2.x, a0.y + a2.y), e2 = make_float2(a0.x - a2.x, a0.y - a2.y);
-  float2 e1 = make_float2(a1.x + w3.x, a1.y + w3.y), e3 = make_float2(a1.x - w3.x, a1.y - w3.y);
-  float2 o0 = make_float2(a4.x + a6.x, a4.y + a6.y), o2 = make_float2(a4.x - a6.x, a4.y - a6.y);
-  float2 o1 = make_float2(a5.x + w7.x, a5.y + w7.y), o3 = make_float2(a5.x - w7.x, a5.y - w7.y);
-  // twiddles w8^k, w8 = e^{SIGN i pi/4}
-  float2 t1 = make_float2(r * (o1.x - SIGN * o1.y), r * (o1.y + SIGN * o1.x));
-  float2 t2 = make_float2(-SIGN * o2.y, SIGN * o2.x);
-  float2 t3 = make_float2(r * (-o3.x - SIGN * o3.y), r * (-o3.y + SIGN * o3.x));
-  v[0] = make_float2(e0.x + o0.x, e0.y + o0.y);
-  v[4] = make_float2(e0.x - o0.x, e0.y - o0.y);
-  v[1] = make_float2(e1.x + t1.x, e1.y + t1.y);
-  v[5] = make_float2(e1.x - t1.x, e1.y - t1.y);
-  v[2] = make_float2(e2.x + t2.x, e2.y + t2.y);
-  v[6] = make_float2(e2.x - t2.x, e2.y - t2.y);
-  v[3] = make_float2(e3.x + t3.x, e3.y + t3.y);
-  v[7] = make_float2(e3.x - t3.x, e3.y - t3.y);
-}
-
-template <int SIGN>
-__device__ __forceinline__ void dft_axis_f(float2* S, const float2* tw, int nk, int len, int stride, int ncol) {
-  const int nlines = (nk / len) * ncol;
-  for (int w = threadIdx.x; w < nlines; w += blockDim.x) {
-    const int cc = w % ncol, line = w / ncol;
-    const int inner = line % stride, outer = line / stride;
-    const int base = outer * stride * len + inner;
-    if (len == 1) continue;
-    if (len == 8) {
-      float2 v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = S[(size_t)(base + j * stride) * ncol + cc];
-      dft8<SIGN>(v);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) S[(size_t)(base + j * stride) * ncol + cc] = v[j];
-      continue;
-    }
-    float2 v[BSE_MAX_NK_AXIS];
-#pragma unroll
-    for (int j = 0; j < BSE_MAX_NK_AXIS; ++j)
-      if (j < len) v[j] = S[(size_t)(base + j * stride) * ncol + cc];
-    for (int qo = 0; qo < len; ++qo) {
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < BSE_MAX_NK_AXIS; ++j) {
-        if (j < len) {
-          float2 t = tw[(j * qo) % len];
-          if (SIGN < 0) t.y = -t.y;
-          acc.x = fmaf(t.x, v[j].x, fmaf(-t.y, v[j].y, acc.x));
-          acc.y = fmaf(t.x, v[j].y, fmaf(t.y, v[j].x, acc.y));
-        }
-      }
-      S[(size_t)(base + qo * stride) * ncol + cc] = acc;
-    }
-  }
-}
-
-// phi[k][c][x] (FP32) -> (1/Nk) F^- W F^+ over the k mesh -> Bphi_k[2c+s][x] (hi, lo)
-// CTA: XC consecutive x, CG consecutive columns; shared S[k][cl*XC + xl].
-__global__ void __launch_bounds__(256) kconv_tc(const float2* __restrict__ phi, const float* __restrict__ w,
-                                                const double* __restrict__ twiddle, __nv_bfloat16* __restrict__ hi,
-                                                __nv_bfloat16* __restrict__ lo, int nk0, int nk1, int nk2, int nx,
-                                                int nc, int xc, int cg, int nnmax) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);   // [3][16]
-  float2* S = tw + 48;
-  const int nk = nk0 * nk1 * nk2;
-  const int ncol = xc * cg;
-  const int x0 = blockIdx.x * xc, c0 = blockIdx.y * cg;
-  for (int i = threadIdx.x; i < 48; i += blockDim.x) tw[i] = make_float2((float)twiddle[2 * i], (float)twiddle[2 * i + 1]);
-  for (int e = threadIdx.x; e < nk * ncol; e += blockDim.x) {
-    const int k = e / ncol, cc = e % ncol, cl = cc / xc, xl = cc % xc;
-    const int c = c0 + cl, x = x0 + xl;
-    S[e] = (c < nc && x < nx) ? phi[((size_t)k * nc + c) * nx + x] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  dft_axis_f<+1>(S, tw + 32, nk, nk2, 1, ncol);
-  __syncthreads();
-  dft_axis_f<+1>(S, tw + 16, nk, nk1, nk2, ncol);
-  __syncthreads();
-  dft_axis_f<+1>(S, tw + 0, nk, nk0, nk1 * nk2, ncol);
-  __syncthreads();
-  const float inv = 1.0f / (float)nk;
-  for (int e = threadIdx.x; e < nk * ncol; e += blockDim.x) {
-    const int r = e / ncol, xl = (e % ncol) % xc, x = x0 + xl;
-    const float wv = (x < nx) ? w[(size_t)r * nx + x] * inv : 0.f;
-    S[e].x *= wv;
-    S[e].y *= wv;
-  }
-  __syncthreads();
-  dft_axis_f<-1>(S, tw + 32, nk, nk2, 1, ncol);
-  __syncthreads();
-  dft_axis_f<-1>(S, tw + 16, nk, nk1, nk2, ncol);
-  __syncthreads();
-  dft_axis_f<-1>(S, tw + 0, nk, nk0, nk1 * nk2, ncol);
-  __syncthreads();
-  // rows j = 2c + s, x contiguous
-  for (int e = threadIdx.x; e < nk * cg * 2 * xc; e += blockDim.x) {
-    const int xl = e % xc, rest = e / xc, s = rest % 2, rest2 = rest / 2, cl = rest2 % cg, k = rest2 / cg;
-    const int c = c0 + cl, x = x0 + xl;
-    if (c < nc && x < nx) {
-      const float2 v = S[(size_t)k * ncol + cl * xc + xl];
-      __nv_bfloat16 h, l;
-      split2(s == 0 ? v.x : v.y, h, l);
-      const size_t o = ((size_t)k * nnmax + 2 * c + s) * nx + x;
-      hi[o] = h;
-      lo[o] = l;
-    }
-  }
-}
-
 // out[c][k][n] = sum_split part + E psi - chi psi + short-range out  (FP64)
 __global__ void g2b_final(const float2* __restrict__ part, int nsplit, const double2* __restrict__ psi,
                           double2* __restrict__ out, const double* __restrict__ e_nk, const double2* __restrict__ chi,
@@ -533,23 +414,26 @@ __global__ void g2b_final(const float2* __restrict__ part, int nsplit, const dou
     }
     const double2 ps = psi[((size_t)c * nk + k) * nb + n];
     const double e = e_nk[kn];
-    double2 val = make_double2(lr.x + e * ps.x, lr.y + e * ps.y);
+    // -chi psi and the short-range projection out in FP32; E psi and the sum in FP64
+    float rx = 0.f, ry = 0.f;
     for (int b = 0; b < na; ++b) {
-      const double2 ch = chi[a * na + b];
-      const double2 pb = psi[((size_t)(v * na + b) * nk + k) * nb + n];
-      val.x -= ch.x * pb.x - ch.y * pb.y;
-      val.y -= ch.x * pb.y + ch.y * pb.x;
+      const double2 chd = chi[a * na + b];
+      const double2 pbd = psi[((size_t)(v * na + b) * nk + k) * nb + n];
+      const float2 ch = make_float2((float)chd.x, (float)chd.y), pb = make_float2((float)pbd.x, (float)pbd.y);
+      rx -= ch.x * pb.x - ch.y * pb.y;
+      ry -= ch.x * pb.y + ch.y * pb.x;
     }
     if (np > 0) {
       const double2* cp = srcp + (size_t)v * na * np + (size_t)a * np;
       for (int p = 0; p < np; ++p) {
-        const double2 ap = a_proj[(size_t)p * nkb + kn];
-        const double2 qq = cp[p];
-        val.x += ap.x * qq.x + ap.y * qq.y;
-        val.y += ap.x * qq.y - ap.y * qq.x;
+        const double2 apd = a_proj[(size_t)p * nkb + kn];
+        const double2 qd = cp[p];
+        const float2 ap = make_float2((float)apd.x, (float)apd.y), qq = make_float2((float)qd.x, (float)qd.y);
+        rx += ap.x * qq.x + ap.y * qq.y;
+        ry += ap.x * qq.y - ap.y * qq.x;
       }
     }
-    out[((size_t)c * nk + k) * nb + n] = val;
+    out[((size_t)c * nk + k) * nb + n] = make_double2(lr.x + (double)rx + e * ps.x, lr.y + (double)ry + e * ps.y);
   }
 }
 
@@ -697,20 +581,8 @@ bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec) {
 
 bse_status bse_kconv_bf16(bse_handle* h, int n_vec) {
   TcState* ts = (TcState*)h->tmap_host;
-  const int nc = n_vec * h->na;
-  const int xc = (h->nx % 16 == 0) ? 16 : 8;
-  int cg = (200 * 1024) / (h->nk * xc * (int)sizeof(float2));
-  if (cg > nc) cg = nc;
-  if (cg < 1) return bse_fail(h, BSE_ERR_UNSUPPORTED, "k mesh too large for the shared-memory k-transform");
-  const size_t smem = (48 + (size_t)h->nk * xc * cg) * sizeof(float2);
-  cudaFuncSetAttribute(kconv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const size_t nbf = (size_t)h->nk * ts->nnmax * h->nx;
-  dim3 g((unsigned)((h->nx + xc - 1) / xc), (unsigned)((nc + cg - 1) / cg));
-  BSE_PROF(h, BSE_K_KCONV,
-           kconv_tc<<<g, 256, smem, h->stream>>>((const float2*)h->phi, (const float*)h->w, h->twiddle, h->bphi,
-                                                 h->bphi + nbf, h->nk3[0], h->nk3[1], h->nk3[2], h->nx, nc, xc, cg,
-                                                 ts->nnmax));
-  return bse_cuda_check(h, cudaGetLastError(), "kconv_tc launch");
+  return bse_kconv_split(h, n_vec, h->bphi, h->bphi + nbf, ts->nnmax);
 }
 
 bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec) {

@@ -202,6 +202,24 @@ def test_l23_matvec_matches_oracle(l23, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
+def test_l23_spectrum_200_steps_within_1e4_of_oracle(l23, prec):
+    """200 plain Haydock steps at full size (the benchmark's recursion): the
+    spectrum is within 1e-4 relative L2 of the stored FP64 oracle spectrum
+    (tests/golden/make_golden.py l23, oracle only) on 2000 omega in [-5, 30] eV."""
+    from pathlib import Path
+    g = np.load(Path(__file__).parent / "golden" / "l23_multiplet_haydock200.npz")
+    s, b = l23
+    sysg = bse.System(s, precision=prec)
+    a, bc, steps, st = sysg.haydock(b[0], 200)
+    assert steps[0] == 200
+    sg = bse.cf_spectrum(a, bc, steps, g["omega"], 0.5)[0]
+    assert rel(sg, g["sigma"]) < 1e-4
+    # the first coefficients precede any loss of orthogonality
+    tol = {"fp64": 1e-9, "fp32": 2e-5, "split_bf16": 1e-4}[prec]
+    assert np.allclose(a[0][:10], g["a"][:10], rtol=tol, atol=tol * 10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
 def test_l23_haydock_prefix_matches_oracle(l23, prec):
     """First 12 Haydock coefficients at full size against the oracle, and the
     12-step spectra within 1e-4 relative L2 (Eq. 1 with Gamma = 0.5 eV)."""
