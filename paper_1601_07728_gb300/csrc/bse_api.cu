@@ -33,13 +33,13 @@ bse_status bse_cuda_check(bse_handle* h, cudaError_t e, const char* what) {
 
 void bse_prof_begin(bse_handle* h, int kind) {
   if (!h->prof || h->ev_used + 2 > h->ev.size()) return;
-  cudaEventRecord(h->ev[h->ev_used], h->stream);
+  cudaEventRecord(h->ev[h->ev_used], h->cur ? h->cur : h->stream);
   h->ev_kind[h->ev_used / 2] = kind;
 }
 
 void bse_prof_end(bse_handle* h) {
   if (!h->prof || h->ev_used + 2 > h->ev.size()) return;
-  cudaEventRecord(h->ev[h->ev_used + 1], h->stream);
+  cudaEventRecord(h->ev[h->ev_used + 1], h->cur ? h->cur : h->stream);
   h->ev_used += 2;
 }
 
@@ -87,6 +87,9 @@ void free_handle(bse_handle* h) {
   if (h->io_out) cudaFree(h->io_out);
   if (h->ws) cudaFree(h->ws);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
 }
 
@@ -171,6 +174,14 @@ bse_status bse_setup(bse_handle** out, const bse_system_desc* d) {
   if (cudaGetDevice(&h->dev) != cudaSuccess) {
     cudaGetLastError();
     h->err = "no CUDA device";
+    free_handle(h);
+    return BSE_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    h->err = "stream/event creation failed";
     free_handle(h);
     return BSE_ERR_CUDA;
   }

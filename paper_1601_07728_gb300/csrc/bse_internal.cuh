@@ -13,6 +13,7 @@
 #define BSE_MAX_ALPHA 16
 #define BSE_MAX_NK_AXIS 16
 #define BSE_MAX_PROJ 64
+#define BSE_FINAL_BLOCKS 512   // blocks per vector of the fused grid->band epilogue
 
 // ---------------------------------------------------------------------------
 // complex helpers (interleaved re, im)
@@ -79,6 +80,11 @@ struct bse_handle {
   void* tmap = nullptr;             // SPLIT_BF16: tensor maps (device copy)
   void* tmap_host = nullptr;
 
+  // side stream for the short-range term (overlaps the band->grid pass)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t cur = nullptr;   // stream the next profiled launch goes to
+
   // grow-only device workspace of the Haydock driver (kept between calls)
   void* ws = nullptr;
   size_t ws_cap = 0;
@@ -123,13 +129,30 @@ bse_status bse_cuda_check(bse_handle* h, cudaError_t e, const char* what);
 // setup kernels (k_setup.cu)
 bse_status bse_setup_device(bse_handle* h, const bse_system_desc* d);
 
-// H psi on device pointers (k_apply.cu); psi/hpsi [n_vec][N] double2, n_vec <= max_vec
-bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, int n_vec);
+// Haydock hook fused into the last kernel of H psi: a[v][i] = Re <psi_v | H psi_v>
+// from per-block partial sums; the last block to finish (counter) reduces them
+// in a fixed order and resets the counter.
+struct bse_dotfuse {
+  double2* partial = nullptr;   // [n_vec][nblk]
+  unsigned* counter = nullptr;
+  double* a = nullptr;          // a[v * a_stride + i]
+  int a_stride = 0, i = 0;
+  const int* active = nullptr;
+  int* status = nullptr;
+};
+
+// H psi on device pointers (k_apply.cu); psi/hpsi [n_vec][N] double2, n_vec <= max_vec.
+// With fuse != nullptr the tensor-core form also produces a_i (returns
+// BSE_ERR_UNSUPPORTED from other forms, whose callers compute it separately).
+bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                            const bse_dotfuse* fuse = nullptr);
+bool bse_apply_fuses_dot(const bse_handle* h);
 
 // tensor-core band<->grid path (k_tc.cu)
 bse_status bse_tc_prepare(bse_handle* h);
 bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec);
-bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec);
+bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                               const bse_dotfuse* fuse, bool wait_side);
 bse_status bse_kconv_bf16(bse_handle* h, int n_vec);
 // k-transform x W (k_kconv.cu): in place on phi[k][c][x], or into bf16 hi/lo planes
 bse_status bse_kconv_inplace(bse_handle* h, int n_vec);

@@ -187,17 +187,27 @@ __global__ void __launch_bounds__(256) sr_in_partial(const double2* __restrict__
   }
 }
 
-// c[o] = sum_b part[b][o]  (fixed order), o over (c, p)
-__global__ void sr_reduce(const double2* __restrict__ part, double2* __restrict__ src, int nblk, int nout) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nout) return;
+// c[o] = sum_b part[b][o], one block of 128 threads per output o (fixed order)
+__global__ void __launch_bounds__(128) sr_reduce(const double2* __restrict__ part, double2* __restrict__ src,
+                                                 int nblk, int nout) {
+  const int o = blockIdx.x;
   double re = 0, im = 0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = threadIdx.x; b < nblk; b += 128) {
     const double2 t = part[(size_t)b * nout + o];
     re += t.x;
     im += t.y;
   }
-  src[o] = make_double2(re, im);
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
+  __shared__ double sr[4], si[4];
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = re;
+    si[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) src[o] = make_double2(sr[0] + sr[1] + sr[2] + sr[3], si[0] + si[1] + si[2] + si[3]);
 }
 
 // c'[v][i] = sum_j M[i][j] c[v][j]: one warp per row i (FP64)
@@ -238,6 +248,7 @@ bse_status apply_simt(bse_handle* h, const double2* psi, double2* hpsi, int n_ve
   }
   bse_status s = bse_kconv_inplace(h, n_vec);
   if (s != BSE_OK) return s;
+  if (h->np > 0) cudaStreamWaitEvent(st, h->ev_join, 0);   // short-range c' ready
   for (int c0 = 0; c0 < nc; c0 += CCG) {
     dim3 g((unsigned)((h->nb + 63) / 64), (unsigned)h->nk);
     BSE_PROF(h, BSE_K_GRID_TO_BAND,
@@ -254,14 +265,20 @@ void launch_sr_in(bse_handle* h, const double2* psi, int nc, int nkb, int nblk) 
   dim3 g((unsigned)nblk, (unsigned)((nc + SRC - 1) / SRC));
   const size_t smem = (size_t)(h->np + SRC) * (SRK + 1) * sizeof(C);
   cudaFuncSetAttribute(sr_in_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  BSE_PROF(h, BSE_K_SR_IN, sr_in_partial<T><<<g, 256, smem, h->stream>>>(h->a_proj, psi, h->sr_part, nkb, h->np, nc));
+  BSE_PROF(h, BSE_K_SR_IN, sr_in_partial<T><<<g, 256, smem, h->side>>>(h->a_proj, psi, h->sr_part, nkb, h->np, nc));
 }
 
 }  // namespace
 
+// Short-range coefficients c' = M (A (x) I) psi on the side stream, forked
+// from and joined back (ev_join) to the handle's stream; the consumer of
+// sr_cp waits on ev_join.
 bse_status bse_sr_terms(bse_handle* h, const double2* psi, int n_vec) {
   if (h->np <= 0) return BSE_OK;
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->side;
+  cudaEventRecord(h->ev_fork, h->stream);
+  cudaStreamWaitEvent(st, h->ev_fork, 0);
+  h->cur = st;
   const int nc = n_vec * h->na;
   const int nkb = h->nk * h->nb;
   const int nblk = (nkb + SRK - 1) / SRK;
@@ -270,25 +287,33 @@ bse_status bse_sr_terms(bse_handle* h, const double2* psi, int n_vec) {
   else
     launch_sr_in<float>(h, psi, nc, nkb, nblk);
   const int nout = nc * h->np;
-  BSE_PROF(h, BSE_K_SR_IN, sr_reduce<<<(nout + 255) / 256, 256, 0, st>>>(h->sr_part, h->sr_c, nblk, nout));
+  BSE_PROF(h, BSE_K_SR_IN, sr_reduce<<<nout, 128, 0, st>>>(h->sr_part, h->sr_c, nblk, nout));
   const int dimm = h->na * h->np;
   dim3 gc((unsigned)((dimm + 7) / 8), (unsigned)n_vec);
   BSE_PROF(h, BSE_K_SR_COUPLE, sr_couple_warp<<<gc, 256, 0, st>>>(h->m_sr, h->sr_c, h->sr_cp, dimm));
+  h->cur = nullptr;
+  cudaEventRecord(h->ev_join, st);
   return bse_cuda_check(h, cudaGetLastError(), "short-range kernels");
 }
 
-bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, int n_vec) {
+bool bse_apply_fuses_dot(const bse_handle* h) { return h->prec == BSE_PREC_SPLIT_BF16; }
+
+bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, int n_vec, const bse_dotfuse* fuse) {
   bse_status s = bse_sr_terms(h, psi, n_vec);
   if (s != BSE_OK) return s;
   switch (h->prec) {
-    case BSE_PREC_FP64: return apply_simt<double>(h, psi, hpsi, n_vec);
-    case BSE_PREC_FP32: return apply_simt<float>(h, psi, hpsi, n_vec);
+    case BSE_PREC_FP64:
+      if (fuse) return BSE_ERR_UNSUPPORTED;
+      return apply_simt<double>(h, psi, hpsi, n_vec);
+    case BSE_PREC_FP32:
+      if (fuse) return BSE_ERR_UNSUPPORTED;
+      return apply_simt<float>(h, psi, hpsi, n_vec);
     case BSE_PREC_SPLIT_BF16: {
       s = bse_tc_band_to_grid(h, psi, n_vec);
       if (s != BSE_OK) return s;
       s = bse_kconv_bf16(h, n_vec);
       if (s != BSE_OK) return s;
-      return bse_tc_grid_to_band(h, psi, hpsi, n_vec);
+      return bse_tc_grid_to_band(h, psi, hpsi, n_vec, fuse, h->np > 0);
     }
     default: return bse_fail(h, BSE_ERR_UNSUPPORTED, "unknown precision");
   }

@@ -493,18 +493,79 @@ __global__ void gm_update_x(const double2* __restrict__ V, long long vstride, co
 }  // namespace
 
 // ---------------------------------------------------------------------------
+namespace {
+// w -= a_i v_i + b_i v_{i-1}; partial |w|^2; the last block (counter) computes
+// b_{i+1} = |w| for every vector in block order, tests breakdown, resets counter.
+__global__ void __launch_bounds__(RB) hay_update_fin(double2* __restrict__ w, const double2* __restrict__ vc,
+                                                     const double2* __restrict__ vp, long long N,
+                                                     const double* __restrict__ a, double* __restrict__ bco,
+                                                     int n_steps, int i, int* __restrict__ active,
+                                                     double2* __restrict__ partial, unsigned* counter, int* steps,
+                                                     int* status) {
+  const int v = blockIdx.y;
+  double acc = 0;
+  if (active[v]) {
+    const double ai = a[(size_t)v * n_steps + i];
+    const double bi = i >= 1 ? bco[(size_t)v * (n_steps + 1) + i] : 0.0;
+    for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < N; e += (long long)gridDim.x * RB) {
+      const size_t o = (size_t)v * N + e;
+      double2 ww = w[o];
+      const double2 c = vc[o];
+      ww.x -= ai * c.x;
+      ww.y -= ai * c.y;
+      if (i >= 1) {
+        const double2 p = vp[o];
+        ww.x -= bi * p.x;
+        ww.y -= bi * p.y;
+      }
+      w[o] = ww;
+      acc += ww.x * ww.x + ww.y * ww.y;
+    }
+  }
+  const double2 s = block_sum2(make_double2(acc, 0.0));
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    partial[(size_t)v * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int vv = 0; vv < (int)gridDim.y; ++vv) {
+    const double2 t = sum_partials(partial, vv, gridDim.x);
+    if (threadIdx.x == 0 && active[vv]) {
+      const double bn = sqrt(t.x);
+      const double ai = a[(size_t)vv * n_steps + i];
+      bco[(size_t)vv * (n_steps + 1) + i + 1] = bn;
+      steps[vv] = i + 1;
+      if (!isfinite(bn) || !isfinite(ai)) {
+        active[vv] = 0;
+        atomicOr(status, ST_NAN);
+      } else if (bn <= 1e-12 * fmax(1.0, fabs(ai))) {
+        active[vv] = 0;
+        atomicOr(status, ST_BREAKDOWN);
+      }
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+}  // namespace
+
 bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_steps, int reorth,
                               double* a_d, double* b_d, int* steps_d) {
   cudaStream_t st = h->stream;
   const long long N = h->N;
   Freer fr;
-  double2 *v3 = nullptr, *partial = nullptr, *basis = nullptr, *coef = nullptr;
+  double2 *v3 = nullptr, *partial = nullptr, *basis = nullptr, *coef = nullptr, *fpart = nullptr;
   int *active = nullptr, *status = nullptr;
+  unsigned* counters = nullptr;
   {
     // three vectors, partial sums, flags: one grow-only workspace kept by the handle
     const size_t bv = 3 * (size_t)n_vec * N * sizeof(double2);
     const size_t bp = (size_t)n_vec * NBLK * sizeof(double2);
-    const size_t need = bv + bp + 256 + (size_t)n_vec * sizeof(int) + 256;
+    const size_t bf = (size_t)n_vec * BSE_FINAL_BLOCKS * sizeof(double2);
+    const size_t need = bv + bp + bf + 256 + (size_t)n_vec * sizeof(int) + 256;
     if (h->ws_cap < need) {
       if (h->ws) cudaFree(h->ws);
       h->ws = nullptr;
@@ -515,10 +576,17 @@ bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_
     char* p = (char*)h->ws;
     v3 = (double2*)p;
     partial = (double2*)(p + bv);
-    status = (int*)(p + bv + bp);
-    active = (int*)(p + bv + bp + 256);
+    fpart = (double2*)(p + bv + bp);
+    status = (int*)(p + bv + bp + bf);
+    counters = (unsigned*)(p + bv + bp + bf + 64);
+    active = (int*)(p + bv + bp + bf + 256);
   }
+  double2* hpart = partial;   // partials of the Haydock reductions
+  // a_i from the fused H psi epilogue when the form supports it and one pass covers all vectors
+  const bool fuse_a = bse_apply_fuses_dot(h) && n_vec <= h->max_vec;
+  const bool fuse_b = !reorth;
   if (reorth) {
+    // Gram-Schmidt partials need one row per basis vector
     TRY(dalloc(h, &partial, (size_t)n_vec * NBLK * (n_steps + 1) * sizeof(double2), "gs partials"));
     fr.add(partial);
     TRY(dalloc(h, &basis, (size_t)n_vec * (n_steps + 1) * N * sizeof(double2), "re-orthogonalisation basis"));
@@ -529,30 +597,45 @@ bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_
   cudaMemsetAsync(a_d, 0, (size_t)n_vec * n_steps * sizeof(double), st);
   cudaMemsetAsync(b_d, 0, (size_t)n_vec * (n_steps + 1) * sizeof(double), st);
   cudaMemsetAsync(steps_d, 0, n_vec * sizeof(int), st);
-  cudaMemsetAsync(status, 0, sizeof(int), st);
+  cudaMemsetAsync(status, 0, 256, st);   // status word and the two last-block counters
   double2* buf[3] = {v3, v3 + (size_t)n_vec * N, v3 + 2 * (size_t)n_vec * N};
   double2 *vp = buf[0], *vc = buf[1], *w = buf[2];
   const dim3 eg = ew_grid(N, n_vec);
   // v_0 = b / |b|
-  BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(b, N, nullptr, 0, N, partial));
-  BSE_PROF(h, BSE_K_RECURSION, hay_init_finalize<<<n_vec, RB, 0, st>>>(partial, NBLK, b_d, n_steps, active, status));
+  BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(b, N, nullptr, 0, N, hpart));
+  BSE_PROF(h, BSE_K_RECURSION, hay_init_finalize<<<n_vec, RB, 0, st>>>(hpart, NBLK, b_d, n_steps, active, status));
   BSE_PROF(h, BSE_K_RECURSION, hay_scale<<<eg, 256, 0, st>>>(b, vc, N, b_d, 0, n_steps + 1, active));
   if (reorth) {
     BSE_PROF(h, BSE_K_RECURSION, copy_vecs<<<eg, 256, 0, st>>>(vc, basis, N, (long long)(n_steps + 1) * N));
   }
   for (int i = 0; i < n_steps; ++i) {
-    TRY(apply_chunked(h, vc, w, n_vec));                       // w = H v_i
-    BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(vc, N, w, N, N, partial));
-    BSE_PROF(h, BSE_K_RECURSION, hay_a_finalize<<<n_vec, RB, 0, st>>>(partial, NBLK, a_d, n_steps, i, active, status));
-    BSE_PROF(h, BSE_K_RECURSION, hay_update<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, vc, vp, N, a_d, b_d, n_steps, i, active, partial));
-    if (reorth) {
+    if (fuse_a) {
+      bse_dotfuse f;
+      f.partial = fpart;
+      f.counter = counters;
+      f.a = a_d;
+      f.a_stride = n_steps;
+      f.i = i;
+      f.active = active;
+      f.status = status;
+      TRY(bse_apply_device(h, vc, w, n_vec, &f));              // w = H v_i, a_i = Re <v_i|w>
+    } else {
+      TRY(apply_chunked(h, vc, w, n_vec));                     // w = H v_i
+      BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(vc, N, w, N, N, hpart));
+      BSE_PROF(h, BSE_K_RECURSION, hay_a_finalize<<<n_vec, RB, 0, st>>>(hpart, NBLK, a_d, n_steps, i, active, status));
+    }
+    if (fuse_b) {
+      BSE_PROF(h, BSE_K_RECURSION,
+               hay_update_fin<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, vc, vp, N, a_d, b_d, n_steps, i, active, hpart,
+                                                                 counters + 1, steps_d, status));
+    } else {
+      BSE_PROF(h, BSE_K_RECURSION, hay_update<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, vc, vp, N, a_d, b_d, n_steps, i, active, hpart));
       TRY(cgs2(h, basis, (long long)(n_steps + 1) * N, w, n_vec, i + 1, partial, coef, n_steps + 1,
                nullptr, 0, active));
-      BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, N, nullptr, 0, N, partial));
+      BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, N, nullptr, 0, N, hpart));
+      BSE_PROF(h, BSE_K_RECURSION, hay_b_finalize<<<n_vec, RB, 0, st>>>(hpart, NBLK, a_d, b_d, n_steps, i, active, steps_d, status));
     }
-    BSE_PROF(h, BSE_K_RECURSION, hay_b_finalize<<<n_vec, RB, 0, st>>>(partial, NBLK, a_d, b_d, n_steps, i, active, steps_d, status));
-    hay_scale<<<eg, 256, 0, st>>>(w, w, N, b_d, i + 1, n_steps + 1, active);   // v_{i+1}
-    BSE_LAUNCHED(h);
+    BSE_PROF(h, BSE_K_RECURSION, hay_scale<<<eg, 256, 0, st>>>(w, w, N, b_d, i + 1, n_steps + 1, active));   // v_{i+1}
     if (reorth && i + 1 <= n_steps) {
       BSE_PROF(h, BSE_K_RECURSION, copy_vecs<<<eg, 256, 0, st>>>(w, basis + (size_t)(i + 1) * N, N, (long long)(n_steps + 1) * N));
     }

@@ -333,11 +333,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int i = 0; i < 16; ++i) pv[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
           const int n = row >> 1;
           if ((lane & 1) == 0 && n < p.nb) {
-            float2* o = p.out + (((size_t)tl.split * p.nk + tl.batch) * p.nb + n) * p.nc;
+            // partials [split][k][c][n]
+            float2* o = p.out + ((size_t)tl.split * p.nk + tl.batch) * p.nc * p.nb + n;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int c = c16 * 8 + i;
-              if (c < p.nc) o[c] = make_float2(v[2 * i] + pv[2 * i + 1], v[2 * i + 1] - pv[2 * i]);
+              if (c < p.nc) o[(size_t)c * p.nb] = make_float2(v[2 * i] + pv[2 * i + 1], v[2 * i + 1] - pv[2 * i]);
             }
           }
         }
@@ -394,21 +395,25 @@ __global__ void prep_bpsi(const double2* __restrict__ psi, __nv_bfloat16* __rest
   }
 }
 
-// out[c][k][n] = sum_split part + E psi - chi psi + short-range out  (FP64)
-__global__ void g2b_final(const float2* __restrict__ part, int nsplit, const double2* __restrict__ psi,
-                          double2* __restrict__ out, const double* __restrict__ e_nk, const double2* __restrict__ chi,
-                          const double2* __restrict__ a_proj, const double2* __restrict__ srcp, int nk, int nb,
-                          int na, int np, int nc) {
+// out[c][k][n] = sum_split part + E psi - chi psi + short-range out.  Grid
+// (blocks per vector, n_vec); with f.partial set, also a[v][i] = Re <psi_v|out_v>.
+__global__ void __launch_bounds__(256) g2b_final(const float2* __restrict__ part, int nsplit,
+                                                 const double2* __restrict__ psi, double2* __restrict__ out,
+                                                 const double* __restrict__ e_nk, const double2* __restrict__ chi,
+                                                 const double2* __restrict__ a_proj, const double2* __restrict__ srcp,
+                                                 int nk, int nb, int na, int np, int nc, bse_dotfuse f) {
   const size_t nkb = (size_t)nk * nb;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < nkb * nc;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % nc);
-    const size_t kn = idx / nc;
+  const int v = blockIdx.y;
+  double dre = 0.0, dim = 0.0;
+  for (size_t e_ = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e_ < (size_t)na * nkb;
+       e_ += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e_ / nkb);
+    const size_t kn = e_ % nkb;
+    const int c = v * na + a;
     const int k = (int)(kn / nb), n = (int)(kn % nb);
-    const int v = c / na, a = c % na;
     double2 lr = make_double2(0, 0);
     for (int sp = 0; sp < nsplit; ++sp) {
-      const float2 t = part[((size_t)sp * nkb + kn) * nc + c];
+      const float2 t = part[(((size_t)sp * nk + k) * nc + c) * nb + n];
       lr.x += t.x;
       lr.y += t.y;
     }
@@ -433,8 +438,55 @@ __global__ void g2b_final(const float2* __restrict__ part, int nsplit, const dou
         ry += ap.x * qq.y - ap.y * qq.x;
       }
     }
-    out[((size_t)c * nk + k) * nb + n] = make_double2(lr.x + (double)rx + e * ps.x, lr.y + (double)ry + e * ps.y);
+    const double2 val = make_double2(lr.x + (double)rx + e * ps.x, lr.y + (double)ry + e * ps.y);
+    out[((size_t)c * nk + k) * nb + n] = val;
+    dre += ps.x * val.x + ps.y * val.y;
+    dim += ps.x * val.y - ps.y * val.x;
   }
+  if (!f.partial) return;
+  // <psi|H psi>: block partial, then the last block reduces all partials in block order
+  __shared__ double sre[8], sim[8];
+  __shared__ int last;
+  for (int off = 16; off > 0; off >>= 1) {
+    dre += __shfl_xor_sync(0xffffffffu, dre, off);
+    dim += __shfl_xor_sync(0xffffffffu, dim, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sre[threadIdx.x >> 5] = dre;
+    sim[threadIdx.x >> 5] = dim;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0, im = 0;
+    for (int w = 0; w < 8; ++w) {
+      r += sre[w];
+      im += sim[w];
+    }
+    f.partial[(size_t)v * gridDim.x + blockIdx.x] = make_double2(r, im);
+    __threadfence();
+    const unsigned prev = atomicAdd(f.counter, 1u);
+    last = prev == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int vv = 0; vv < (int)gridDim.y; ++vv) {
+    double r = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) r += f.partial[(size_t)vv * gridDim.x + b].x;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sre[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int w = 0; w < 8; ++w) s += sre[w];
+      if (f.active[vv]) {
+        f.a[(size_t)vv * f.a_stride + f.i] = s;
+        if (!isfinite(s)) atomicOr(f.status, 2);
+      }
+    }
+  }
+  if (threadIdx.x == 0) *f.counter = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -585,7 +637,8 @@ bse_status bse_kconv_bf16(bse_handle* h, int n_vec) {
   return bse_kconv_split(h, n_vec, h->bphi, h->bphi + nbf, ts->nnmax);
 }
 
-bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec) {
+bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                               const bse_dotfuse* fuse, bool wait_side) {
   TcState* ts = (TcState*)h->tmap_host;
   const int nc = n_vec * h->na;
   const int nn = round_up(2 * nc, 16);
@@ -610,12 +663,15 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   p.nc = nc;
   bse_status s = launch_gemm(h, ts, 1, ts->a6_hi, ts->a6_lo, b_hi, b_lo, p, BSE_K_GRID_TO_BAND);
   if (s != BSE_OK) return s;
-  const size_t total = (size_t)h->nk * h->nb * nc;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 4096) blocks = 4096;
+  if (wait_side) cudaStreamWaitEvent(h->stream, h->ev_join, 0);   // short-range c' ready
+  const size_t per_vec = (size_t)h->na * h->nk * h->nb;
+  int blocks = (int)((per_vec + 255) / 256);
+  if (blocks > BSE_FINAL_BLOCKS) blocks = BSE_FINAL_BLOCKS;
+  bse_dotfuse f = fuse ? *fuse : bse_dotfuse();
   BSE_PROF(h, BSE_K_PREP,
-           g2b_final<<<blocks, 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
-                                                    h->a_proj, h->sr_cp, h->nk, h->nb, h->na, h->np, nc));
+           g2b_final<<<dim3((unsigned)blocks, (unsigned)n_vec), 256, 0, h->stream>>>(
+               (const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi, h->a_proj, h->sr_cp, h->nk, h->nb, h->na,
+               h->np, nc, f));
   return bse_cuda_check(h, cudaGetLastError(), "g2b_final launch");
 }
 

@@ -66,6 +66,22 @@ def test_apply_h_split_bf16_matches_oracle(kw):
         assert rel(out[v], ref[v]) < TOL["split_bf16"]
 
 
+@pytest.mark.parametrize("max_vec", [3, 2])
+def test_haydock_batched_vectors_split_bf16(max_vec):
+    """Three start vectors (polarisations) in one Haydock call: fused epilogue
+    dot when one pass covers all vectors (max_vec = 3), separate reductions when
+    the batch is chunked (max_vec = 2); each equals the oracle's single run."""
+    s = S.tiny_system(46, n_alpha=6, nk=(4, 4, 4), n_bands=24, nx=(8, 8, 4), n_proj=4)
+    b = S.make_start_vectors(s, 3, seed=2)
+    sysg = bse.System(s, precision="split_bf16", max_vec=max_vec)
+    a, bc, steps, st = sysg.haydock(b, 10)
+    for v in range(3):
+        ao, bo, _, _ = O.haydock(lambda x: O.apply_h(s, x), b[v], 10)
+        assert steps[v] == 10
+        assert np.allclose(a[v], ao, rtol=1e-4, atol=1e-3)
+        assert np.allclose(bc[v], bo, rtol=1e-4, atol=1e-3)
+
+
 def test_apply_h_device_pointers():
     torch = pytest.importorskip("torch")
     s = S.tiny_system(30, n_alpha=6, nk=(2, 2, 2), n_bands=12, nx=(6, 6, 6), n_proj=4)
