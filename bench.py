@@ -214,7 +214,9 @@ def main():
 
     s = S.make_system(args.workload)
     b = S.make_start_vectors(s, 1)[0]
-    stream = torch.cuda.current_stream()
+    # a dedicated (capturable) stream: the library records each Haydock run as one CUDA graph
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     sysg = bse.System(s, precision=args.precision, max_vec=1, stream=stream.cuda_stream)
     n = sysg.dim
     db = torch.from_numpy(b).to("cuda")

@@ -395,6 +395,120 @@ __global__ void prep_bpsi(const double2* __restrict__ psi, __nv_bfloat16* __rest
   }
 }
 
+// Block-level <psi|H psi> partial + last-block reduction shared by both epilogues.
+__device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
+  __shared__ double sre[8], sim[8];
+  __shared__ int last;
+  for (int off = 16; off > 0; off >>= 1) {
+    dre += __shfl_xor_sync(0xffffffffu, dre, off);
+    dim += __shfl_xor_sync(0xffffffffu, dim, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sre[threadIdx.x >> 5] = dre;
+    sim[threadIdx.x >> 5] = dim;
+  }
+  __syncthreads();
+  const int v = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double r = 0, im = 0;
+    for (int w = 0; w < 8; ++w) {
+      r += sre[w];
+      im += sim[w];
+    }
+    f.partial[(size_t)v * gridDim.x + blockIdx.x] = make_double2(r, im);
+    __threadfence();
+    const unsigned prev = atomicAdd(f.counter, 1u);
+    last = prev == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int vv = 0; vv < (int)gridDim.y; ++vv) {
+    double r = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) r += f.partial[(size_t)vv * gridDim.x + b].x;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sre[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int w = 0; w < 8; ++w) s += sre[w];
+      if (f.active[vv]) {
+        f.a[(size_t)vv * f.a_stride + f.i] = s;
+        if (!isfinite(s)) atomicOr(f.status, 2);
+      }
+    }
+  }
+  if (threadIdx.x == 0) *f.counter = 0u;
+}
+
+// Epilogue with NA core states per thread: one thread per (k, n) of vector
+// v = blockIdx.y computes all NA outputs, so A[:, kn] and psi[v][:][kn] are
+// read once; c' and chi are staged in shared memory as FP32.
+template <int NA>
+__global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ part, int nsplit,
+                                                    const double2* __restrict__ psi, double2* __restrict__ out,
+                                                    const double* __restrict__ e_nk, const double2* __restrict__ chi,
+                                                    const double2* __restrict__ a_proj,
+                                                    const double2* __restrict__ srcp, int nk, int nb, int np, int nc,
+                                                    bse_dotfuse f) {
+  __shared__ float2 cps[NA * BSE_MAX_PROJ];
+  __shared__ float2 chs[NA * NA];
+  const size_t nkb = (size_t)nk * nb;
+  const int v = blockIdx.y;
+  for (int i = threadIdx.x; i < NA * np; i += blockDim.x) {
+    const double2 q = srcp[(size_t)v * NA * np + i];
+    cps[i] = make_float2((float)q.x, (float)q.y);
+  }
+  for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) chs[i] = make_float2((float)chi[i].x, (float)chi[i].y);
+  __syncthreads();
+  double dre = 0.0, dim = 0.0;
+  for (size_t kn = blockIdx.x * (size_t)blockDim.x + threadIdx.x; kn < nkb; kn += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(kn / nb), n = (int)(kn % nb);
+    double2 ps[NA];
+    float2 pf[NA], acc[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      ps[a] = psi[(size_t)(v * NA + a) * nkb + kn];
+      pf[a] = make_float2((float)ps[a].x, (float)ps[a].y);
+      acc[a] = make_float2(0.f, 0.f);
+    }
+    for (int p = 0; p < np; ++p) {
+      const double2 apd = a_proj[(size_t)p * nkb + kn];
+      const float2 ap = make_float2((float)apd.x, (float)apd.y);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        const float2 q = cps[a * np + p];
+        acc[a].x += ap.x * q.x + ap.y * q.y;   // conj(A) c'
+        acc[a].y += ap.x * q.y - ap.y * q.x;
+      }
+    }
+    const double e = e_nk[kn];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      float rx = acc[a].x, ry = acc[a].y;
+#pragma unroll
+      for (int b = 0; b < NA; ++b) {
+        const float2 ch = chs[a * NA + b];
+        rx -= ch.x * pf[b].x - ch.y * pf[b].y;
+        ry -= ch.x * pf[b].y + ch.y * pf[b].x;
+      }
+      const int c = v * NA + a;
+      double lx = 0.0, ly = 0.0;
+      for (int sp = 0; sp < nsplit; ++sp) {
+        const float2 t = part[(((size_t)sp * nk + k) * nc + c) * nb + n];
+        lx += t.x;
+        ly += t.y;
+      }
+      const double2 val = make_double2(lx + (double)rx + e * ps[a].x, ly + (double)ry + e * ps[a].y);
+      out[(size_t)c * nkb + kn] = val;
+      dre += ps[a].x * val.x + ps[a].y * val.y;
+      dim += ps[a].x * val.y - ps[a].y * val.x;
+    }
+  }
+  if (f.partial) fused_dot_tail(f, dre, dim);
+}
+
 // out[c][k][n] = sum_split part + E psi - chi psi + short-range out.  Grid
 // (blocks per vector, n_vec); with f.partial set, also a[v][i] = Re <psi_v|out_v>.
 __global__ void __launch_bounds__(256) g2b_final(const float2* __restrict__ part, int nsplit,
@@ -443,50 +557,7 @@ __global__ void __launch_bounds__(256) g2b_final(const float2* __restrict__ part
     dre += ps.x * val.x + ps.y * val.y;
     dim += ps.x * val.y - ps.y * val.x;
   }
-  if (!f.partial) return;
-  // <psi|H psi>: block partial, then the last block reduces all partials in block order
-  __shared__ double sre[8], sim[8];
-  __shared__ int last;
-  for (int off = 16; off > 0; off >>= 1) {
-    dre += __shfl_xor_sync(0xffffffffu, dre, off);
-    dim += __shfl_xor_sync(0xffffffffu, dim, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    sre[threadIdx.x >> 5] = dre;
-    sim[threadIdx.x >> 5] = dim;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = 0, im = 0;
-    for (int w = 0; w < 8; ++w) {
-      r += sre[w];
-      im += sim[w];
-    }
-    f.partial[(size_t)v * gridDim.x + blockIdx.x] = make_double2(r, im);
-    __threadfence();
-    const unsigned prev = atomicAdd(f.counter, 1u);
-    last = prev == gridDim.x * gridDim.y - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int vv = 0; vv < (int)gridDim.y; ++vv) {
-    double r = 0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) r += f.partial[(size_t)vv * gridDim.x + b].x;
-    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sre[threadIdx.x >> 5] = r;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0;
-      for (int w = 0; w < 8; ++w) s += sre[w];
-      if (f.active[vv]) {
-        f.a[(size_t)vv * f.a_stride + f.i] = s;
-        if (!isfinite(s)) atomicOr(f.status, 2);
-      }
-    }
-  }
-  if (threadIdx.x == 0) *f.counter = 0u;
+  if (f.partial) fused_dot_tail(f, dre, dim);
 }
 
 // ---------------------------------------------------------------------------
@@ -668,10 +739,24 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   int blocks = (int)((per_vec + 255) / 256);
   if (blocks > BSE_FINAL_BLOCKS) blocks = BSE_FINAL_BLOCKS;
   bse_dotfuse f = fuse ? *fuse : bse_dotfuse();
-  BSE_PROF(h, BSE_K_PREP,
-           g2b_final<<<dim3((unsigned)blocks, (unsigned)n_vec), 256, 0, h->stream>>>(
-               (const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi, h->a_proj, h->sr_cp, h->nk, h->nb, h->na,
-               h->np, nc, f));
+  const size_t nkb = (size_t)h->nk * h->nb;
+  int bk = (int)((nkb + 255) / 256);
+  if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
+  const dim3 gk((unsigned)bk, (unsigned)n_vec);
+  if (h->na == 6) {
+    BSE_PROF(h, BSE_K_PREP,
+             g2b_final_na<6><<<gk, 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
+                                                        h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
+  } else if (h->na == 1) {
+    BSE_PROF(h, BSE_K_PREP,
+             g2b_final_na<1><<<gk, 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
+                                                        h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
+  } else {
+    BSE_PROF(h, BSE_K_PREP,
+             g2b_final<<<dim3((unsigned)blocks, (unsigned)n_vec), 256, 0, h->stream>>>(
+                 (const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi, h->a_proj, h->sr_cp, h->nk, h->nb,
+                 h->na, h->np, nc, f));
+  }
   return bse_cuda_check(h, cudaGetLastError(), "g2b_final launch");
 }
 

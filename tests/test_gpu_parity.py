@@ -82,6 +82,24 @@ def test_haydock_batched_vectors_split_bf16(max_vec):
         assert np.allclose(bc[v], bo, rtol=1e-4, atol=1e-3)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_haydock_on_capturable_stream_matches_oracle(prec):
+    """On a non-default stream the step loop runs as one captured CUDA graph;
+    the coefficients must equal the oracle's exactly as the eager loop does."""
+    torch = pytest.importorskip("torch")
+    s = S.tiny_system(47, n_alpha=6, nk=(2, 2, 2), n_bands=20, nx=(8, 4, 4), n_proj=3)
+    b = S.make_start_vectors(s, 2, seed=3)
+    stream = torch.cuda.Stream()
+    sysg = bse.System(s, precision=prec, max_vec=2, stream=stream.cuda_stream)
+    a, bc, steps, st = sysg.haydock(b, 25)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    for v in range(2):
+        ao, bo, _, _ = O.haydock(lambda x: O.apply_h(s, x), b[v], 25)
+        assert steps[v] == 25
+        assert np.allclose(a[v][:20], ao[:20], rtol=tol, atol=tol * 10)
+        assert np.allclose(bc[v][:21], bo[:21], rtol=tol, atol=tol * 10)
+
+
 def test_apply_h_device_pointers():
     torch = pytest.importorskip("torch")
     s = S.tiny_system(30, n_alpha=6, nk=(2, 2, 2), n_bands=12, nx=(6, 6, 6), n_proj=4)
