@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--gmres-omega", type=int, default=40, help="shifts in the GMRES measurement (0 = skip)")
+    p.add_argument("--gmres-max-iter", type=int, default=2000)
+    p.add_argument("--gmres-chunk", type=int, default=10, help="systems per batched H application")
     return p.parse_args()
 
 
@@ -279,6 +282,36 @@ def main():
     steps_done = int(st_d.item())
     value = world * steps_done / (t_max / 1e3)
 
+    # GMRES: (H - omega - i Gamma) x = b for n_omega shifts, all advanced together
+    gm = None
+    if args.gmres_omega > 0:
+        n_om = args.gmres_omega
+        zs = np.linspace(-5.0, 30.0, n_om) + 0.5j
+        sys_g = bse.System(s, precision=args.precision, max_vec=args.gmres_chunk, stream=stream.cuda_stream)
+        xg = torch.empty((n_om, n), dtype=torch.complex128, device="cuda")
+        sys_g.gmres(db, zs[:2], rtol=1e-3, restart=30, max_iter=60, precond="none", x=xg[:2])   # warm-up
+        gm = {"n_omega": n_om, "rtol": 1e-6, "restart": 30, "max_iter": args.gmres_max_iter,
+              "shifts": "omega in linspace(-5, 30, %d) eV + 0.5i" % n_om, "chunk": args.gmres_chunk}
+        for pc in ("none", "jacobi"):
+            torch.cuda.synchronize()
+            barrier()
+            l1 = sys_g.launches
+            g0 = time.perf_counter()
+            _, g_it, g_rr, g_st = sys_g.gmres(db, zs, rtol=1e-6, restart=30, max_iter=args.gmres_max_iter,
+                                              precond=pc, x=xg)
+            torch.cuda.synchronize()
+            g_el = time.perf_counter() - g0
+            if dist is not None:
+                t = torch.tensor([g_el], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                g_el = float(t.item())
+            conv = int(np.sum(g_rr <= 1e-6))
+            gm[pc] = {"solves_per_s": world * conv / g_el, "seconds": g_el, "converged": conv,
+                      "iters_mean": float(np.mean(g_it)), "iters_max": int(np.max(g_it)),
+                      "max_rel_resid": float(np.max(g_rr)), "gpu_launches": sys_g.launches - l1}
+        sys_g.close()
+        del xg
+
     # end to end: the public call with pinned host buffers, H2D + D2H every step
     hp = torch.from_numpy(b).pin_memory()
     ho = torch.empty_like(hp).pin_memory()
@@ -338,6 +371,7 @@ def main():
             "e2e": {"value": e2e, "unit": "matvecs/s", "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16,
                     "api": "bse_apply_h with pinned host psi/hpsi"},
             "gpu_launches": launches,
+            "gmres": gm,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

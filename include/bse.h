@@ -139,12 +139,21 @@ bse_status bse_cf_spectrum(const double* a, const double* bcoef, const int* step
                            int n_stride, const double* omega, int n_omega, double gamma,
                            int terminator, double* sigma);
 
-/* Preconditioner choice for bse_gmres. */
+/* Preconditioner choice for bse_gmres (low byte of `precond`).  On the shifted
+ * Hermitian operator H - z with Re z inside the spectrum a Jacobi right
+ * preconditioner can slow GMRES down; NONE is often the better default. */
 typedef enum { BSE_PRECOND_NONE = 0, BSE_PRECOND_JACOBI = 1 } bse_precond;
+
+/* Flag or-ed into `precond`: x holds the initial guess x_0 on entry (else
+ * x_0 = 0).  Restarted GMRES carries only x between cycles, so calling with
+ * max_iter = restart and this flag repeatedly reproduces one solve cycle by
+ * cycle. */
+#define BSE_GMRES_X0 0x100
 
 /* Restarted right-preconditioned GMRES(restart) for (H - z_j) x_j = b, one
  * system per complex shift z_j = omega_j + i*Gamma_j, all n_z systems advanced
- * together (their H applications are batched).  x_0 = 0; Arnoldi by classical
+ * together (their H applications are batched; systems that have converged
+ * drop out of the batch).  x_0 = 0 (or x on entry with BSE_GMRES_X0); Arnoldi by classical
  * Gram-Schmidt applied twice in FP64; Givens least squares; convergence when
  * the true residual |b - (H - z)x|/|b| <= rtol (recomputed at each restart and
  * at exit).  b [N], z [n_z] (bse_c128), x [n_z][N], iters [n_z] (H

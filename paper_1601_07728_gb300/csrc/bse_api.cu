@@ -168,7 +168,6 @@ bse_status bse_setup(bse_handle** out, const bse_system_desc* d) {
   h->N = (long long)h->na * h->nk * h->nb;
   h->stream = (cudaStream_t)d->stream;
   if (h->prec == BSE_PREC_SPLIT_BF16) {
-    if (h->nx % 8 != 0) return bad("split-bf16 form needs Nx divisible by 8");
     if ((long long)h->max_vec * h->na * 2 > 256) return bad("split-bf16 form needs 2*max_vec*n_alpha <= 256");
   }
   if (cudaGetDevice(&h->dev) != cudaSuccess) {
@@ -280,7 +279,8 @@ bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_
   if (!h) return BSE_ERR_INVALID_ARG;
   if (!b || !z || !x || !iters || !rel_resid || n_z < 1 || restart < 1 || max_iter < 1 || !(rtol > 0))
     return bse_fail(h, BSE_ERR_INVALID_ARG, "gmres: bad arguments");
-  if (precond != BSE_PRECOND_NONE && precond != BSE_PRECOND_JACOBI)
+  const int pkind = precond & 0xff;
+  if ((precond & ~(0xff | BSE_GMRES_X0)) != 0 || (pkind != BSE_PRECOND_NONE && pkind != BSE_PRECOND_JACOBI))
     return bse_fail(h, BSE_ERR_INVALID_ARG, "gmres: unknown preconditioner");
   Staged sb, sz, sx, si, sr;
   TRY(stage_in(h, sb, b, (size_t)h->N * sizeof(double2), true, "b"));

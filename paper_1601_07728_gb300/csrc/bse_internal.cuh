@@ -64,9 +64,9 @@ struct bse_handle {
   // band<->grid operands
   void* u = nullptr;          // FP64: double2 [Nk][Nx][Nb]; FP32: float2; phase folded
   void* w = nullptr;          // [Nk][Nx] double (FP64) or float
-  __nv_bfloat16* u_hi = nullptr;   // SPLIT_BF16: [Nk][Nx][2Nb] (re, im interleaved)
+  __nv_bfloat16* u_hi = nullptr;   // SPLIT_BF16: [Nk][Nx][Kp] (re, im interleaved, Kp = 2Nb padded to 8)
   __nv_bfloat16* u_lo = nullptr;
-  __nv_bfloat16* ut_hi = nullptr;  // SPLIT_BF16: [Nk][2Nb][Nx] (transposed copy)
+  __nv_bfloat16* ut_hi = nullptr;  // SPLIT_BF16: K-tiled transposed copy [Nk][ceil(Nx/64)][2Nb][64]
   __nv_bfloat16* ut_lo = nullptr;
 
   // scratch sized for max_vec columns
@@ -75,7 +75,7 @@ struct bse_handle {
   double2* sr_cp = nullptr;   // [max_vec][Na*Np]
   double2* sr_part = nullptr; // [ceil(Nk*Nb/64)][max_vec*Na][Np] split-K partial projections
   __nv_bfloat16* bpsi = nullptr;    // SPLIT_BF16: [Nk][2][Nrow][2Nb] B operand of band->grid
-  __nv_bfloat16* bphi = nullptr;    // SPLIT_BF16: [Nk][2][Nrow][Nx]  B operand of grid->band
+  __nv_bfloat16* bphi = nullptr;    // SPLIT_BF16: hi/lo K-tiled [Nk][ceil(Nx/64)][Nrow][64] B operand of grid->band
   float* part = nullptr;            // SPLIT_BF16: split-K partial tiles
   void* tmap = nullptr;             // SPLIT_BF16: tensor maps (device copy)
   void* tmap_host = nullptr;

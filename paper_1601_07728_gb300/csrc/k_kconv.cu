@@ -117,24 +117,31 @@ __global__ void __launch_bounds__(256) kconv_cubic(typename CT<T>::t* __restrict
   }
   const size_t colstride = (size_t)nc * nx;   // distance between consecutive k in phi
   C* base = phi + (size_t)c * nx + x;
-  // pass A: global load + forward transform along axis 2 (k = (m0 N + m1) N + m2)
+  // pass A: global load (all of this thread's pencils first, so the loads are
+  // in flight together) + forward transform along axis 2 (k = (m0 N + m1) N + m2)
+  {
+    C va[PPT][N];
 #pragma unroll
-  for (int i = 0; i < PPT; ++i) {
-    const int p = g + 16 * i;
-    if (p < NP) {
-      C v[N];
+    for (int i = 0; i < PPT; ++i) {
+      const int p = g + 16 * i;
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        if (xin) {
-          v[j] = base[(size_t)(p * N + j) * colstride];
+        if (xin && p < NP) {
+          va[i][j] = base[(size_t)(p * N + j) * colstride];
         } else {
-          v[j].x = 0;
-          v[j].y = 0;
+          va[i][j].x = 0;
+          va[i][j].y = 0;
         }
       }
-      dftN<T, N, +1>(v, tw);
+    }
 #pragma unroll
-      for (int j = 0; j < N; ++j) S[(p * N + j) * XC + xl] = v[j];
+    for (int i = 0; i < PPT; ++i) {
+      const int p = g + 16 * i;
+      if (p < NP) {
+        dftN<T, N, +1>(va[i], tw);
+#pragma unroll
+        for (int j = 0; j < N; ++j) S[(p * N + j) * XC + xl] = va[i][j];
+      }
     }
   }
   __syncthreads();
@@ -155,6 +162,13 @@ __global__ void __launch_bounds__(256) kconv_cubic(typename CT<T>::t* __restrict
   __syncthreads();
   // pass C: forward along axis 0, times W(x, R)/Nk, inverse along axis 0; p = (m1, m2): k = j N^2 + p
   const T inv = (T)1 / (T)NK;
+  T wr[PPT][N];   // W(x, R) of this thread's pencils, loaded ahead of the transforms
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + 16 * i;
+#pragma unroll
+    for (int j = 0; j < N; ++j) wr[i][j] = (xin && p < NP) ? w[(size_t)(j * NP + p) * nx + x] * inv : (T)0;
+  }
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
     const int p = g + 16 * i;
@@ -165,9 +179,8 @@ __global__ void __launch_bounds__(256) kconv_cubic(typename CT<T>::t* __restrict
       dftN<T, N, +1>(v, tw);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        const T wv = xin ? w[(size_t)(j * NP + p) * nx + x] * inv : (T)0;
-        v[j].x *= wv;
-        v[j].y *= wv;
+        v[j].x *= wr[i][j];
+        v[j].y *= wr[i][j];
       }
       dftN<T, N, -1>(v, tw);
 #pragma unroll
@@ -204,14 +217,15 @@ __global__ void __launch_bounds__(256) kconv_cubic(typename CT<T>::t* __restrict
         for (int j = 0; j < N; ++j) {
           const int k = p * N + j;
           if constexpr (BF16) {
-            const size_t o = ((size_t)k * nnmax + 2 * c) * nx + x;
+            // K-tiled planes [k][x/64][row][64], rows 2c (re) and 2c+1 (im)
+            const size_t o = (((size_t)k * ((nx + 63) >> 6) + (x >> 6)) * nnmax + 2 * c) * 64 + (x & 63);
             __nv_bfloat16 h0, l0, h1, l1;
             split_bf((float)v[j].x, h0, l0);
             split_bf((float)v[j].y, h1, l1);
             hi[o] = h0;
             lo[o] = l0;
-            hi[o + nx] = h1;
-            lo[o + nx] = l1;
+            hi[o + 64] = h1;
+            lo[o + 64] = l1;
           } else {
             base[(size_t)k * colstride] = v[j];
           }
@@ -302,14 +316,14 @@ __global__ void __launch_bounds__(256) kconv_generic(typename CT<T>::t* __restri
     const int k = e / XC, x = x0 + e % XC;
     if (x >= nx) continue;
     if constexpr (BF16) {
-      const size_t o = ((size_t)k * nnmax + 2 * c) * nx + x;
+      const size_t o = (((size_t)k * ((nx + 63) >> 6) + (x >> 6)) * nnmax + 2 * c) * 64 + (x & 63);
       __nv_bfloat16 h0, l0, h1, l1;
       split_bf((float)S[e].x, h0, l0);
       split_bf((float)S[e].y, h1, l1);
       hi[o] = h0;
       lo[o] = l0;
-      hi[o + nx] = h1;
-      lo[o + nx] = l1;
+      hi[o + 64] = h1;
+      lo[o + 64] = l1;
     } else {
       phi[(size_t)k * colstride + (size_t)c * nx + x] = S[e];
     }

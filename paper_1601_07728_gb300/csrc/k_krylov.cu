@@ -259,13 +259,59 @@ bse_status apply_chunked(bse_handle* h, const double2* in, double2* out, int n_v
 }
 
 // CGS2: for pass in 0,1: coef = basis^H w; w -= basis coef; hacc += coef.
+// Gram-Schmidt projections <basis_j|w> for JB basis vectors at a time: w is
+// read once per group of JB (not once per basis vector).  partial[v][j][blk].
+constexpr int GS_JB = 8;
+__global__ void __launch_bounds__(RB) gs_dot_multi(const double2* __restrict__ basis, long long bstride,
+                                                   const double2* __restrict__ w, long long N, int nj,
+                                                   double2* __restrict__ partial, const int* __restrict__ mask) {
+  const int v = blockIdx.y;
+  const bool on = !mask || mask[v];
+  const double2* bv = basis + (size_t)v * bstride;
+  const double2* wv = w + (size_t)v * N;
+  __shared__ double2 sred[RB / 32][GS_JB];
+  for (int j0 = 0; j0 < nj; j0 += GS_JB) {
+    double2 acc[GS_JB];
+#pragma unroll
+    for (int q = 0; q < GS_JB; ++q) acc[q] = make_double2(0, 0);
+    if (on) {
+      for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < N; e += (long long)gridDim.x * RB) {
+        const double2 b = wv[e];
+#pragma unroll
+        for (int q = 0; q < GS_JB; ++q) {
+          if (j0 + q < nj) {
+            const double2 a = bv[(size_t)(j0 + q) * N + e];
+            acc[q].x += a.x * b.x + a.y * b.y;
+            acc[q].y += a.x * b.y - a.y * b.x;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < GS_JB; ++q) {
+      for (int off = 16; off > 0; off >>= 1) {
+        acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
+        acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
+      }
+      if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < GS_JB && j0 + threadIdx.x < nj) {
+      double2 s = make_double2(0, 0);
+      for (int wq = 0; wq < RB / 32; ++wq) s = cadd(s, sred[wq][threadIdx.x]);
+      partial[((size_t)v * nj + j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
 bse_status cgs2(bse_handle* h, const double2* basis, long long bstride, double2* w, int nv, int nj,
                 double2* partial, double2* coef, int coef_stride, double2* hacc, int hacc_stride,
                 const int* mask) {
   cudaStream_t st = h->stream;
   const long long N = h->N;
   for (int pass = 0; pass < 2; ++pass) {
-    BSE_PROF(h, BSE_K_RECURSION, gs_dot_partial<<<dim3(NBLK, nj, nv), RB, 0, st>>>(basis, bstride, w, N, partial));
+    BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(NBLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask));
     BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, NBLK, coef, coef_stride, hacc, hacc_stride));
     BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask));
   }
@@ -371,6 +417,33 @@ __global__ void gm_precond(const double2* __restrict__ V, long long vstride, dou
     double2 a = vv[e];
     if (jacobi) a = cdiv(a, make_double2(d[e] - zv.x, -zv.y));
     T[(size_t)v * N + e] = a;
+  }
+}
+
+// compact form for the still-active systems: slot s holds system idx[s]
+// T[s] = P V_j[idx[s]]
+__global__ void gm_precond_c(const double2* __restrict__ V, long long vstride, double2* __restrict__ T, long long N,
+                             const double* __restrict__ d, const double2* __restrict__ z, int jacobi,
+                             const int* __restrict__ idx) {
+  const int s = blockIdx.y, v = idx[s];
+  const double2 zv = z[v];
+  const double2* vv = V + (size_t)v * vstride;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    double2 a = vv[e];
+    if (jacobi) a = cdiv(a, make_double2(d[e] - zv.x, -zv.y));
+    T[(size_t)s * N + e] = a;
+  }
+}
+
+// W[idx[s]] = Wc[s] - z[idx[s]] T[s]
+__global__ void gm_scatter_shift(const double2* __restrict__ Wc, const double2* __restrict__ T,
+                                 const double2* __restrict__ z, double2* __restrict__ W, long long N,
+                                 const int* __restrict__ idx) {
+  const int s = blockIdx.y, v = idx[s];
+  const double2 zv = z[v];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    const double2 t = T[(size_t)s * N + e], w = Wc[(size_t)s * N + e];
+    W[(size_t)v * N + e] = make_double2(w.x - (zv.x * t.x - zv.y * t.y), w.y - (zv.x * t.y + zv.y * t.x));
   }
 }
 
@@ -704,7 +777,7 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
   cudaStream_t st = h->stream;
   const long long N = h->N;
   const int m = restart;
-  const int jac = precond == BSE_PRECOND_JACOBI;
+  const int jac = (precond & 0xff) == BSE_PRECOND_JACOBI;
   Freer fr;
   double2 *V, *T, *W, *partial, *Hs, *sn, *g, *y, *coef;
   double *cs, *beta, *hnorm, *est;
@@ -726,6 +799,11 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
   TRY(dalloc(h, &active, (size_t)n_z * sizeof(int), "active")); fr.add(active);
   TRY(dalloc(h, &jdone, (size_t)n_z * sizeof(int), "jdone")); fr.add(jdone);
   TRY(dalloc(h, &mask, (size_t)n_z * sizeof(int), "mask")); fr.add(mask);
+  double2* Wc;
+  int* didx;
+  TRY(dalloc(h, &Wc, (size_t)n_z * N * sizeof(double2), "gmres packed H T")); fr.add(Wc);
+  TRY(dalloc(h, &didx, (size_t)n_z * sizeof(int), "active index")); fr.add(didx);
+  std::vector<int> hidx(n_z);
 
   double bnorm = 0;
   {
@@ -737,14 +815,16 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
     bnorm = sqrt(bnorm);
   }
   if (!(bnorm > 0) || !isfinite(bnorm)) return bse_fail(h, BSE_ERR_INVALID_ARG, "b must be nonzero and finite");
-  cudaMemsetAsync(x, 0, (size_t)n_z * N * sizeof(double2), st);
+  const bool x0 = (precond & BSE_GMRES_X0) != 0;   // x holds the initial guess
+  if (!x0) cudaMemsetAsync(x, 0, (size_t)n_z * N * sizeof(double2), st);
   cudaMemsetAsync(iters_d, 0, n_z * sizeof(int), st);
   const dim3 eg = ew_grid(N, n_z);
   std::vector<int> hact(n_z);
   for (int cycle = 0;; ++cycle) {
     // true residual r = b - (H - z) x into V_0, |r|, activity
-    if (cycle > 0) TRY(apply_chunked(h, x, W, n_z));
-    BSE_PROF(h, BSE_K_RECURSION, gm_residual<<<eg, 256, 0, st>>>(b, W, x, z, V, vstride, N, cycle == 0));
+    const bool zero_x = cycle == 0 && !x0;
+    if (!zero_x) TRY(apply_chunked(h, x, W, n_z));
+    BSE_PROF(h, BSE_K_RECURSION, gm_residual<<<eg, 256, 0, st>>>(b, W, x, z, V, vstride, N, zero_x));
     BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_z), RB, 0, st>>>(V, vstride, nullptr, 0, N, partial));
     BSE_PROF(h, BSE_K_RECURSION, gm_beta<<<n_z, RB, 0, st>>>(partial, NBLK, bnorm, rtol, max_iter, iters_d, beta, rel_d, active, g, m));
     TRY(bse_cuda_check(h, cudaMemcpyAsync(hact.data(), active, n_z * sizeof(int), cudaMemcpyDeviceToHost, st), "active copy"));
@@ -759,9 +839,15 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
     BSE_PROF(h, BSE_K_RECURSION, gm_next<<<eg, 256, 0, st>>>(V, vstride, V, vstride, N, beta, active));
     for (int j = 0; j < m; ++j) {
       cudaMemcpyAsync(mask, active, n_z * sizeof(int), cudaMemcpyDeviceToDevice, st);
-      BSE_PROF(h, BSE_K_RECURSION, gm_precond<<<eg, 256, 0, st>>>(V + (size_t)j * N, vstride, T, N, h->jdiag, z, jac));
-      TRY(apply_chunked(h, T, W, n_z));
-      BSE_PROF(h, BSE_K_RECURSION, gm_shift<<<eg, 256, 0, st>>>(W, T, z, N));
+      // H is applied to the still-active systems only, packed into nact slots
+      int ns = 0;
+      for (int v = 0; v < n_z; ++v)
+        if (hact[v]) hidx[ns++] = v;
+      TRY(bse_cuda_check(h, cudaMemcpyAsync(didx, hidx.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st), "idx"));
+      const dim3 ec(eg.x, (unsigned)ns);
+      BSE_PROF(h, BSE_K_RECURSION, gm_precond_c<<<ec, 256, 0, st>>>(V + (size_t)j * N, vstride, T, N, h->jdiag, z, jac, didx));
+      TRY(apply_chunked(h, T, Wc, ns));
+      BSE_PROF(h, BSE_K_RECURSION, gm_scatter_shift<<<ec, 256, 0, st>>>(Wc, T, z, W, N, didx));
       TRY(cgs2(h, V, vstride, W, n_z, j + 1, partial, coef, m + 1, Hs + (size_t)j * (m + 1),
                (m + 1) * m, mask));
       BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_z), RB, 0, st>>>(W, N, nullptr, 0, N, partial));

@@ -64,7 +64,8 @@ __global__ void split_rows_kernel(const double2* __restrict__ u, __nv_bfloat16* 
   }
 }
 
-// u [Nk][Nx][Nb] complex -> hi/lo [Nk][2Nb][Nx] (transposed, x contiguous)
+// u [Nk][Nx][Nb] complex -> hi/lo K-tiled transpose [Nk][ceil(Nx/64)][2Nb][64]:
+// element (k, row 2n+u, x) at ((k*X64 + x/64)*2Nb + row)*64 + x%64 (x padding zeroed by the caller)
 __global__ void split_transpose_kernel(const double2* __restrict__ u, __nv_bfloat16* __restrict__ hi,
                                        __nv_bfloat16* __restrict__ lo, int nx, int nb) {
   __shared__ double2 tile[32][33];
@@ -80,9 +81,10 @@ __global__ void split_transpose_kernel(const double2* __restrict__ u, __nv_bfloa
     int n = n0 + r, x = x0 + threadIdx.x;
     if (n < nb && x < nx) {
       double2 v = tile[threadIdx.x][r];
-      size_t base = (size_t)k * 2 * nb * nx;
-      split_bf16(v.x, hi[base + (size_t)(2 * n) * nx + x], lo[base + (size_t)(2 * n) * nx + x]);
-      split_bf16(v.y, hi[base + (size_t)(2 * n + 1) * nx + x], lo[base + (size_t)(2 * n + 1) * nx + x]);
+      const size_t x64 = (size_t)(nx + 63) / 64;
+      const size_t o = (((size_t)k * x64 + x / 64) * (2 * (size_t)nb) + 2 * n) * 64 + (x % 64);
+      split_bf16(v.x, hi[o], lo[o]);
+      split_bf16(v.y, hi[o + 64], lo[o + 64]);
     }
   }
 }
@@ -240,8 +242,12 @@ bse_status bse_setup_device(bse_handle* h, const bse_system_desc* d) {
         const size_t nrp = (size_t)h->nk * h->nx * kp;
         if ((s = dev_alloc(h, &h->u_hi, nrp * sizeof(__nv_bfloat16), "u_hi")) != BSE_OK) break;
         if ((s = dev_alloc(h, &h->u_lo, nrp * sizeof(__nv_bfloat16), "u_lo")) != BSE_OK) break;
-        if ((s = dev_alloc(h, &h->ut_hi, nr * sizeof(__nv_bfloat16), "ut_hi")) != BSE_OK) break;
-        if ((s = dev_alloc(h, &h->ut_lo, nr * sizeof(__nv_bfloat16), "ut_lo")) != BSE_OK) break;
+        const size_t ntp = (size_t)h->nk * ((h->nx + 63) / 64) * 64 * 2 * h->nb;   // K-tiled, x padded to 64
+        (void)nr;
+        if ((s = dev_alloc(h, &h->ut_hi, ntp * sizeof(__nv_bfloat16), "ut_hi")) != BSE_OK) break;
+        if ((s = dev_alloc(h, &h->ut_lo, ntp * sizeof(__nv_bfloat16), "ut_lo")) != BSE_OK) break;
+        cudaMemsetAsync(h->ut_hi, 0, ntp * sizeof(__nv_bfloat16), st);
+        cudaMemsetAsync(h->ut_lo, 0, ntp * sizeof(__nv_bfloat16), st);
         BSE_PROF(h, BSE_K_PREP, split_rows_kernel<<<4096, 256, 0, st>>>(u64, h->u_hi, h->u_lo, (size_t)h->nk * h->nx, h->nb, kp));
         dim3 gt((unsigned)((h->nx + 31) / 32), (unsigned)((h->nb + 31) / 32), (unsigned)h->nk);
         BSE_PROF(h, BSE_K_PREP, split_transpose_kernel<<<gt, dim3(32, 8), 0, st>>>(u64, h->ut_hi, h->ut_lo, h->nx, h->nb));

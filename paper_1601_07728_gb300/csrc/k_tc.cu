@@ -79,6 +79,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
 }
@@ -233,11 +242,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         const uint32_t st = sbase + (uint32_t)s * stage_bytes;
         mbar_expect_tx(full(s), stage_bytes);
-        const int kc = (tl.kb0 + kb) * TC_KB;
-        tma_load_3d(st, &ma_hi, full(s), kc, tl.mt * TC_M, tl.batch);
-        tma_load_3d(st + a_bytes, &ma_lo, full(s), kc, tl.mt * TC_M, tl.batch);
-        tma_load_3d(st + 2 * a_bytes, &mb_hi, full(s), kc, 0, tl.batch);
-        tma_load_3d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), kc, 0, tl.batch);
+        if (p.mode == 0) {
+          // row-major operands [batch][rows][K]: K block = 64 consecutive elements of each row
+          const int kc = (tl.kb0 + kb) * TC_KB;
+          tma_load_3d(st, &ma_hi, full(s), kc, tl.mt * TC_M, tl.batch);
+          tma_load_3d(st + a_bytes, &ma_lo, full(s), kc, tl.mt * TC_M, tl.batch);
+          tma_load_3d(st + 2 * a_bytes, &mb_hi, full(s), kc, 0, tl.batch);
+          tma_load_3d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), kc, 0, tl.batch);
+        } else {
+          // K-tiled operands [batch][K/64][rows][64]: one contiguous block per K block
+          const int kt = tl.kb0 + kb;
+          tma_load_4d(st, &ma_hi, full(s), 0, tl.mt * TC_M, kt, tl.batch);
+          tma_load_4d(st + a_bytes, &ma_lo, full(s), 0, tl.mt * TC_M, kt, tl.batch);
+          tma_load_4d(st + 2 * a_bytes, &mb_hi, full(s), 0, 0, kt, tl.batch);
+          tma_load_4d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), 0, 0, kt, tl.batch);
+        }
         *(volatile int*)issued = it + 1;
       }
     }
@@ -399,6 +418,7 @@ __global__ void prep_bpsi(const double2* __restrict__ psi, __nv_bfloat16* __rest
 __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
   __shared__ double sre[8], sim[8];
   __shared__ int last;
+  const int nw = blockDim.x >> 5;   // warps per block (<= 8)
   for (int off = 16; off > 0; off >>= 1) {
     dre += __shfl_xor_sync(0xffffffffu, dre, off);
     dim += __shfl_xor_sync(0xffffffffu, dim, off);
@@ -411,7 +431,7 @@ __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
   const int v = blockIdx.y;
   if (threadIdx.x == 0) {
     double r = 0, im = 0;
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < nw; ++w) {
       r += sre[w];
       im += sim[w];
     }
@@ -432,7 +452,7 @@ __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0;
-      for (int w = 0; w < 8; ++w) s += sre[w];
+      for (int w = 0; w < nw; ++w) s += sre[w];
       if (f.active[vv]) {
         f.a[(size_t)vv * f.a_stride + f.i] = s;
         if (!isfinite(s)) atomicOr(f.status, 2);
@@ -473,13 +493,29 @@ __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ p
       pf[a] = make_float2((float)ps[a].x, (float)ps[a].y);
       acc[a] = make_float2(0.f, 0.f);
     }
-    for (int p = 0; p < np; ++p) {
+    int p = 0;
+    for (; p + 4 <= np; p += 4) {
+      double2 apd[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) apd[u] = a_proj[(size_t)(p + u) * nkb + kn];   // 4 loads in flight
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 ap = make_float2((float)apd[u].x, (float)apd[u].y);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          const float2 q = cps[a * np + p + u];
+          acc[a].x += ap.x * q.x + ap.y * q.y;   // conj(A) c'
+          acc[a].y += ap.x * q.y - ap.y * q.x;
+        }
+      }
+    }
+    for (; p < np; ++p) {
       const double2 apd = a_proj[(size_t)p * nkb + kn];
       const float2 ap = make_float2((float)apd.x, (float)apd.y);
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
         const float2 q = cps[a * np + p];
-        acc[a].x += ap.x * q.x + ap.y * q.y;   // conj(A) c'
+        acc[a].x += ap.x * q.x + ap.y * q.y;
         acc[a].y += ap.x * q.y - ap.y * q.x;
       }
     }
@@ -597,6 +633,23 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, u
   return r == CUDA_SUCCESS;
 }
 
+// 4-D bf16 map of a K-tiled array [batch][ktiles][rows][64] (row stride 64
+// elements, tile stride rows_stride*64, batch stride ktiles*rows_stride*64);
+// box {64, box_rows, 1, 1} = one contiguous block, 128-byte swizzle.
+bool make_map_tiled(CUtensorMap* m, const void* base, uint64_t rows, uint64_t rows_stride, uint64_t ktiles,
+                    uint64_t batch, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)TC_KB, rows, ktiles, batch};
+  cuuint64_t strides[3] = {(cuuint64_t)TC_KB * 2, rows_stride * TC_KB * 2, ktiles * rows_stride * TC_KB * 2};
+  cuuint32_t box[4] = {(cuuint32_t)TC_KB, box_rows, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 struct TcState {
   int kp = 0, nnmax = 0, smax = 0, sms = 0;
   int* err = nullptr;   // device error word
@@ -646,7 +699,8 @@ bse_status bse_tc_prepare(bse_handle* h) {
   while (units * sp < 8 * ts->sms && kbt / (sp * 2) >= 8) sp *= 2;
   ts->smax = sp;
   const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
-  const size_t nbf = (size_t)h->nk * ts->nnmax * h->nx;
+  const size_t x64 = (size_t)(h->nx + TC_KB - 1) / TC_KB;
+  const size_t nbf = (size_t)h->nk * x64 * ts->nnmax * TC_KB;   // K-tiled [k][x/64][row][64]
   if (cudaMalloc((void**)&h->bpsi, 2 * nbp * sizeof(__nv_bfloat16)) != cudaSuccess ||
       cudaMalloc((void**)&h->bphi, 2 * nbf * sizeof(__nv_bfloat16)) != cudaSuccess ||
       cudaMalloc((void**)&h->part, (size_t)ts->smax * h->nk * h->nb * h->na * h->max_vec * sizeof(float2)) !=
@@ -661,8 +715,8 @@ bse_status bse_tc_prepare(bse_handle* h) {
   const int kp = ts->kp;
   bool ok = make_map(&ts->a2_hi, h->u_hi, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
             make_map(&ts->a2_lo, h->u_lo, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
-            make_map(&ts->a6_hi, h->ut_hi, h->nx, 2 * h->nb, h->nk, h->nx, (uint64_t)2 * h->nb * h->nx, TC_M) &&
-            make_map(&ts->a6_lo, h->ut_lo, h->nx, 2 * h->nb, h->nk, h->nx, (uint64_t)2 * h->nb * h->nx, TC_M);
+            make_map_tiled(&ts->a6_hi, h->ut_hi, 2 * h->nb, 2 * h->nb, x64, h->nk, TC_M) &&
+            make_map_tiled(&ts->a6_lo, h->ut_lo, 2 * h->nb, 2 * h->nb, x64, h->nk, TC_M);
   if (!ok) return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
   return bse_cuda_check(h, cudaStreamSynchronize(h->stream), "tc prepare");
 }
@@ -704,7 +758,7 @@ bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec) {
 
 bse_status bse_kconv_bf16(bse_handle* h, int n_vec) {
   TcState* ts = (TcState*)h->tmap_host;
-  const size_t nbf = (size_t)h->nk * ts->nnmax * h->nx;
+  const size_t nbf = (size_t)h->nk * ((h->nx + TC_KB - 1) / TC_KB) * ts->nnmax * TC_KB;
   return bse_kconv_split(h, n_vec, h->bphi, h->bphi + nbf, ts->nnmax);
 }
 
@@ -713,10 +767,11 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   TcState* ts = (TcState*)h->tmap_host;
   const int nc = n_vec * h->na;
   const int nn = round_up(2 * nc, 16);
-  const size_t nbf = (size_t)h->nk * ts->nnmax * h->nx;
+  const size_t x64 = (size_t)(h->nx + TC_KB - 1) / TC_KB;
+  const size_t nbf = (size_t)h->nk * x64 * ts->nnmax * TC_KB;
   CUtensorMap b_hi, b_lo;
-  if (!make_map(&b_hi, h->bphi, h->nx, nn, h->nk, h->nx, (uint64_t)ts->nnmax * h->nx, nn) ||
-      !make_map(&b_lo, h->bphi + nbf, h->nx, nn, h->nk, h->nx, (uint64_t)ts->nnmax * h->nx, nn))
+  if (!make_map_tiled(&b_hi, h->bphi, nn, ts->nnmax, x64, h->nk, nn) ||
+      !make_map_tiled(&b_lo, h->bphi + nbf, nn, ts->nnmax, x64, h->nk, nn))
     return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
   TcParams p{};
   p.mode = 1;
@@ -740,17 +795,17 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   if (blocks > BSE_FINAL_BLOCKS) blocks = BSE_FINAL_BLOCKS;
   bse_dotfuse f = fuse ? *fuse : bse_dotfuse();
   const size_t nkb = (size_t)h->nk * h->nb;
-  int bk = (int)((nkb + 255) / 256);
+  int bk = (int)((nkb + 63) / 64);   // 64-thread blocks: more blocks in flight for this latency-bound pass
   if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
   const dim3 gk((unsigned)bk, (unsigned)n_vec);
   if (h->na == 6) {
     BSE_PROF(h, BSE_K_PREP,
-             g2b_final_na<6><<<gk, 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
-                                                        h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
+             g2b_final_na<6><<<gk, 64, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
+                                                       h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
   } else if (h->na == 1) {
     BSE_PROF(h, BSE_K_PREP,
-             g2b_final_na<1><<<gk, 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
-                                                        h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
+             g2b_final_na<1><<<gk, 64, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
+                                                       h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
   } else {
     BSE_PROF(h, BSE_K_PREP,
              g2b_final<<<dim3((unsigned)blocks, (unsigned)n_vec), 256, 0, h->stream>>>(

@@ -50,6 +50,9 @@ TC_SHAPES = [
     dict(seed=43, n_alpha=2, nk=(8, 1, 3), n_bands=70, nx=(10, 4, 3), n_proj=3),
     dict(seed=44, n_alpha=6, nk=(4, 4, 4), n_bands=64, nx=(16, 16, 4), n_proj=2),
     dict(seed=45, n_alpha=3, nk=(1, 1, 1), n_bands=1, nx=(2, 2, 2), n_proj=1),
+    # grid sizes that are not multiples of 8 (x padding of the K-tiled operands)
+    dict(seed=48, n_alpha=6, nk=(3, 3, 3), n_bands=13, nx=(5, 3, 7), n_proj=2),
+    dict(seed=49, n_alpha=1, nk=(5, 5, 5), n_bands=40, nx=(13, 1, 5), n_proj=0),
 ]
 
 
@@ -251,6 +254,28 @@ def test_l23_spectrum_200_steps_within_1e4_of_oracle(l23, prec):
     # the first coefficients precede any loss of orthogonality
     tol = {"fp64": 1e-9, "fp32": 2e-5, "split_bf16": 1e-4}[prec]
     assert np.allclose(a[0][:10], g["a"][:10], rtol=tol, atol=tol * 10)
+
+
+@pytest.mark.parametrize("prec,res_tol", [("fp64", 2e-6), ("split_bf16", 1e-4)])
+def test_l23_gmres_full_size(l23, prec, res_tol):
+    """GMRES at full size: the oracle recomputes the true FP64 residual of the
+    returned x, and sigma(omega) = Im<b|x>/pi matches the stored oracle Haydock
+    spectrum (200 steps, converged at Gamma = 0.5 eV) at the same omega."""
+    from pathlib import Path
+    g = np.load(Path(__file__).parent / "golden" / "l23_multiplet_haydock200.npz")
+    s, b = l23
+    oms = np.array([g["omega"][400], g["omega"][900], g["omega"][1300]])   # ~2, 10.8, 17.8 eV
+    sysg = bse.System(s, precision=prec, max_vec=3)
+    # unpreconditioned: on this shifted Hermitian operator a Jacobi right
+    # preconditioner slows GMRES(30) down several-fold (interior shifts)
+    x, it, rr, st = sysg.gmres(b[0], oms + 0.5j, rtol=1e-6, restart=30, max_iter=3000, precond="none")
+    assert st == bse.BSE_OK and np.all(rr <= 1e-6)
+    for j, om in enumerate(oms):
+        r = b[0] - (O.apply_h(s, x[j]) - (om + 0.5j) * x[j])
+        assert np.linalg.norm(r) / np.linalg.norm(b[0]) < res_tol
+        sig = np.imag(np.vdot(b[0], x[j])) / np.pi
+        ref = O.cf_spectrum(g["a"], g["b"], np.array([om]), 0.5)[0]
+        assert abs(sig - ref) < 1e-3 * abs(ref)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
