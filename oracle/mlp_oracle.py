@@ -1,0 +1,186 @@
+"""FP64 oracle of the learned GMRES preconditioner (test infrastructure only).
+
+TEST INFRASTRUCTURE ONLY: used by the test-suite, never by the product path.
+
+The paper has no preconditioner (it uses Haydock, Sec. 3.2); GMRES for
+(H - z) x = b with z = omega + i Gamma applies the resolvent of Eq. 2 to one
+vector.  The learned preconditioner is defined here step by step so the CUDA
+kernels can be checked against it:
+
+  rows j = (alpha, n, k) of the exciton vector (Eq. 8); per row and shift z
+  features f_j (12 numbers, see ``features``) -> 3-layer network, width 128,
+  SiLU activations, FP16-rounded weights -> 34 outputs o_j:
+      sigma_j = i*ETA0 + SHIFT * (o_j0 + i o_j1)             (eV)
+      p_j     = 1 / (D_j - z - sigma_j)      D = diag(H) (Jacobi diagonal)
+      U_jq    = o_j(2+q)  + i o_j(10+q),   V_jq = o_j(18+q) + i o_j(26+q),  q < 8
+  P r = p (.) r + U (V^H r) / N                (diagonal + rank 8)
+  loss over (residual r_t, error e_t) pairs of a solve: sum_t |P r_t - e_t|^2 / |e_t|^2.
+
+With the last layer zero, P is the damped diagonal 1/(D - omega - i(Gamma +
+ETA0)).  Gradients are by hand-written backpropagation and are pinned against
+central finite differences in the test-suite.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+F_IN, WIDTH, F_OUT, RANK = 12, 128, 34, 8
+ETA0 = 4.5      # eV, damping of the initial diagonal
+SHIFT = 5.0     # eV per unit of the shift outputs
+MAX_ALPHA = 6   # one-hot width of the core-state feature
+
+PARAM_SHAPES = [("w1", (F_IN, WIDTH)), ("b1", (WIDTH,)), ("w2", (WIDTH, WIDTH)), ("b2", (WIDTH,)),
+                ("w3", (WIDTH, F_OUT)), ("b3", (F_OUT,))]
+
+
+def n_params():
+    return int(sum(np.prod(s) for _, s in PARAM_SHAPES))
+
+
+def unpack(flat):
+    out, o = {}, 0
+    for name, shp in PARAM_SHAPES:
+        n = int(np.prod(shp))
+        out[name] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shp)
+        o += n
+    return out
+
+
+def pack(params):
+    return np.concatenate([params[name].reshape(-1) for name, _ in PARAM_SHAPES])
+
+
+def fp16(params):
+    """The function the GPU evaluates: every parameter rounded to FP16."""
+    return {k: v.astype(np.float16).astype(np.float64) for k, v in params.items()}
+
+
+def features(diag, e_nk, chi_diag, a_norm, n_alpha, omega, gamma):
+    """Per-row features, [N][12] with N = Na*Nk*Nb rows in [alpha][k][n] order:
+      0 (D_j - omega)/10        1 gamma
+      2 (E_nk - omega)/10       3 D_j - E_nk + chi_aa   (interaction part of the diagonal)
+      4 chi_aa / 5              5 |A_{:,nk}|  (local-basis weight of the band state)
+      6..11 one-hot alpha (alpha >= 6 folded into 5)."""
+    na = n_alpha
+    nkb = e_nk.size
+    d = diag.reshape(na, nkb)
+    x = np.zeros((na, nkb, F_IN))
+    for a in range(na):
+        x[a, :, 0] = (d[a] - omega) / 10.0
+        x[a, :, 1] = gamma
+        x[a, :, 2] = (e_nk.reshape(-1) - omega) / 10.0
+        x[a, :, 3] = d[a] - e_nk.reshape(-1) + chi_diag[a]
+        x[a, :, 4] = chi_diag[a] / 5.0
+        x[a, :, 5] = a_norm.reshape(-1)
+        x[a, :, 6 + min(a, MAX_ALPHA - 1)] = 1.0
+    return x.reshape(na * nkb, F_IN)
+
+
+def system_features(s, diag, omega, gamma):
+    """features() for a synth.BSESystem and its Jacobi diagonal."""
+    a_norm = np.zeros(s.n_k * s.n_bands) if s.a_proj is None else \
+        np.sqrt((np.abs(s.a_proj.reshape(s.n_proj, -1)) ** 2).sum(0))
+    return features(diag, s.e_nk, np.real(np.diag(s.chi)), a_norm, s.n_alpha, omega, gamma)
+
+
+def silu(x):
+    return x / (1.0 + np.exp(-x))
+
+
+def dsilu(x):
+    sg = 1.0 / (1.0 + np.exp(-x))
+    return sg + x * sg * (1.0 - sg)
+
+
+def forward(params, x):
+    """o = W3^T silu(W2^T silu(W1^T x + b1) + b2) + b3 for every row; returns (o, cache)."""
+    z1 = x @ params["w1"] + params["b1"]
+    h1 = silu(z1)
+    z2 = h1 @ params["w2"] + params["b2"]
+    h2 = silu(z2)
+    o = h2 @ params["w3"] + params["b3"]
+    return o, (x, z1, h1, z2, h2)
+
+
+def assemble(o, diag, z):
+    """(p, U, V) of P = diag(p) + U V^H / N from the network outputs."""
+    sigma = 1j * ETA0 + SHIFT * (o[:, 0] + 1j * o[:, 1])
+    p = 1.0 / (diag - z - sigma)
+    u = o[:, 2:2 + RANK] + 1j * o[:, 2 + RANK:2 + 2 * RANK]
+    v = o[:, 2 + 2 * RANK:2 + 3 * RANK] + 1j * o[:, 2 + 3 * RANK:2 + 4 * RANK]
+    return p, u, v
+
+
+def apply(p, u, v, r):
+    """P r = p (.) r + U (V^H r) / N."""
+    return p * r + u @ (v.conj().T @ r) / r.shape[0]
+
+
+def loss(params, x, diag, z, rs, es, quantize=True):
+    """sum_t |P r_t - e_t|^2 / |e_t|^2 with the FP16-rounded network
+    (quantize=False evaluates the FP64 network as given)."""
+    o, _ = forward(fp16(params) if quantize else params, x)
+    p, u, v = assemble(o, diag, z)
+    tot = 0.0
+    for r, e in zip(rs, es):
+        d = apply(p, u, v, r) - e
+        tot += float(np.vdot(d, d).real / np.vdot(e, e).real)
+    return tot
+
+
+def grad(params, x, diag, z, rs, es, quantize=True):
+    """(loss, dloss/dparams) by backpropagation through assemble and the network.
+
+    With delta_t = P r_t - e_t, w_t = 2/|e_t|^2, c_t = V^H r_t / N and
+    lambda_t = U^H delta_t (complex gradients g with dL = Re sum conj(g) dX):
+      g_p = sum_t w_t delta_t conj(r_t);   g_U = sum_t w_t delta_t c_t^H;
+      g_V = sum_t w_t r_t lambda_t^H / N;  dp = p^2 dsigma, dsigma = SHIFT (do0 + i do1)."""
+    q16 = fp16(params) if quantize else params
+    o, (x_, z1, h1, z2, h2) = forward(q16, x)
+    p, u, v = assemble(o, diag, z)
+    n = x.shape[0]
+    g_p = np.zeros(n, dtype=np.complex128)
+    g_u = np.zeros((n, RANK), dtype=np.complex128)
+    g_v = np.zeros((n, RANK), dtype=np.complex128)
+    tot = 0.0
+    for r, e in zip(rs, es):
+        c = v.conj().T @ r / n
+        d = p * r + u @ c - e
+        w = 2.0 / np.vdot(e, e).real
+        tot += 0.5 * w * np.vdot(d, d).real
+        g_p += w * d * np.conj(r)
+        g_u += w * np.outer(d, np.conj(c))
+        lam = u.conj().T @ d
+        g_v += w * np.outer(r, np.conj(lam)) / n
+    gs = np.conj(g_p) * p * p                                # dL = Re(conj(g_p) p^2 dsigma)
+    do = np.zeros_like(o)
+    do[:, 0] = SHIFT * np.real(gs)
+    do[:, 1] = -SHIFT * np.imag(gs)
+    do[:, 2:2 + RANK] = g_u.real
+    do[:, 2 + RANK:2 + 2 * RANK] = g_u.imag
+    do[:, 2 + 2 * RANK:2 + 3 * RANK] = g_v.real
+    do[:, 2 + 3 * RANK:2 + 4 * RANK] = g_v.imag
+    gr = {}
+    gr["w3"] = h2.T @ do
+    gr["b3"] = do.sum(0)
+    dh2 = do @ q16["w3"].T
+    dz2 = dh2 * dsilu(z2)
+    gr["w2"] = h1.T @ dz2
+    gr["b2"] = dz2.sum(0)
+    dh1 = dz2 @ q16["w2"].T
+    dz1 = dh1 * dsilu(z1)
+    gr["w1"] = x_.T @ dz1
+    gr["b1"] = dz1.sum(0)
+    return tot, gr
+
+
+def adam(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (t counts from 1); returns new (params, m, v)."""
+    newp, newm, newv = {}, {}, {}
+    for k in params:
+        newm[k] = beta1 * m[k] + (1 - beta1) * grads[k]
+        newv[k] = beta2 * v[k] + (1 - beta2) * grads[k] ** 2
+        mh = newm[k] / (1 - beta1 ** t)
+        vh = newv[k] / (1 - beta2 ** t)
+        newp[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+    return newp, newm, newv

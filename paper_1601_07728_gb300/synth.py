@@ -240,6 +240,39 @@ def omega_grid(n: int = 2000, lo: float = -5.0, hi: float = 30.0) -> np.ndarray:
     return np.linspace(lo, hi, n)
 
 
+MLP_SHAPES = [((12, 128), "w1"), ((128,), "b1"), ((128, 128), "w2"), ((128,), "b2"), ((128, 34), "w3"),
+              ((34,), "b3")]
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the preconditioner network, packed as
+    w1 [12][128], b1, w2 [128][128], b2, w3 [128][34], b3 (float32).
+    Hidden weights ~ N(0, 1/fan_in); the last layer is zero except the eight
+    V-factor outputs' imaginary/real columns (18..33), which start small so
+    that the rank-8 term has a gradient."""
+    rng = rng_for(77, seed, STREAM_SITE)
+    parts = []
+    for shp, name in MLP_SHAPES:
+        if name == "w1":
+            parts.append(rng.standard_normal(shp) / np.sqrt(12.0))
+        elif name == "w2":
+            parts.append(rng.standard_normal(shp) / np.sqrt(128.0))
+        elif name == "w3":
+            w = np.zeros(shp)
+            w[:, 18:34] = rng.standard_normal((128, 16)) * 0.05 / np.sqrt(128.0)
+            parts.append(w)
+        else:
+            parts.append(np.zeros(shp))
+    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+
+
+def reduced_l23(seed: int = 0) -> BSESystem:
+    """A seeded smaller variant of the L2,3 multiplet workload (4^3 k, 32
+    bands, 8^3 grid, same physics) used to train the preconditioner."""
+    return make_system("l23_multiplet", site=seed,
+                       overrides=dict(nk=(4, 4, 4), n_bands=32, nx=(8, 8, 8)))
+
+
 def tiny_system(seed: int, n_alpha=2, nk=(2, 1, 3), n_bands=3, nx=(2, 3, 2), *,
                 n_proj=2, cell=7.4, eps=5.0, kshift=(0.0, 0.0, 0.0),
                 w_const=None, so=True, m_scale=0.5) -> BSESystem:
