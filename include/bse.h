@@ -127,6 +127,20 @@ bse_status bse_apply_h(bse_handle* h, const bse_c128* psi, bse_c128* hpsi, int n
 bse_status bse_haydock(bse_handle* h, const bse_c128* b, int n_vec, int n_steps, int reorth,
                        double* a, double* bcoef, int* steps_done);
 
+/* Haydock runs of several absorbing sites at once (the per-site averaging of
+ * Sec. 4.5).  hs[s] are independent handles (uneven sizes allowed), each
+ * created with its own non-NULL stream; every site runs bse_haydock's
+ * recursion (no re-orthogonalisation) on n_vec start vectors b[s].  All sites
+ * are recorded into one CUDA graph -- a fork from a master stream to every
+ * site stream, each site's full run, a join -- launched once, so kernels of
+ * different sites overlap.  If the streams are not capturable (NULL or shared)
+ * the sites run one after another.  Outputs per site as for bse_haydock;
+ * site_status [n_sites] (host) receives each site's status; the return value
+ * is the worst status other than BSE_ERR_BREAKDOWN. */
+bse_status bse_haydock_batch(bse_handle* const* hs, const bse_c128* const* b, int n_sites, int n_vec,
+                             int n_steps, double* const* a, double* const* bcoef, int* const* steps_done,
+                             int* site_status);
+
 /* Loss function from Haydock coefficients (Eqs. 1-2):
  *   sigma(omega) = -(1/pi) b_0^2 Im g(omega + i*gamma),
  *   g(z) = 1/(z - a_0 - b_1^2/(z - a_1 - ... - b_{n-1}^2/(z - a_{n-1} - t))),
@@ -142,7 +156,7 @@ bse_status bse_cf_spectrum(const double* a, const double* bcoef, const int* step
 /* Preconditioner choice for bse_gmres (low byte of `precond`).  On the shifted
  * Hermitian operator H - z with Re z inside the spectrum a Jacobi right
  * preconditioner can slow GMRES down; NONE is often the better default. */
-typedef enum { BSE_PRECOND_NONE = 0, BSE_PRECOND_JACOBI = 1 } bse_precond;
+typedef enum { BSE_PRECOND_NONE = 0, BSE_PRECOND_JACOBI = 1, BSE_PRECOND_MLP = 2 } bse_precond;
 
 /* Flag or-ed into `precond`: x holds the initial guess x_0 on entry (else
  * x_0 = 0).  Restarted GMRES carries only x between cycles, so calling with
@@ -163,6 +177,55 @@ typedef enum { BSE_PRECOND_NONE = 0, BSE_PRECOND_JACOBI = 1 } bse_precond;
 bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_z, double rtol,
                      int restart, int max_iter, int precond, bse_c128* x, int* iters,
                      double* rel_resid);
+
+/* ---- learned GMRES preconditioner (no counterpart in the paper) ----------
+ * For every row j = (alpha, n, k) and shift z = omega + i*Gamma, 12 features
+ *   (D_j-omega)/10, Gamma, (E_nk-omega)/10, D_j-E_nk+chi_aa, chi_aa/5,
+ *   |A_{:,nk}|, one-hot alpha (6)          (D = diag(H) of bse_jacobi_diag)
+ * pass a network dense(12,128)-SiLU-dense(128,128)-SiLU-dense(128,34) with FP16
+ * weights and FP32 accumulation; its outputs o give
+ *   p_j = 1/(D_j - z - sigma_j), sigma_j = i*4.5 eV + 5 eV*(o_0 + i o_1),
+ *   U_jq = o_{2+q} + i o_{10+q},  V_jq = o_{18+q} + i o_{26+q}  (q < 8),
+ * and GMRES uses the right preconditioner P = diag(p) + U V^H / N.  Parameters
+ * are packed w1[12][128], b1[128], w2[128][128], b2[128], w3[128][34], b3[34]
+ * (bse_mlp_n_params() floats, FP32 master copy).  Training minimises the
+ * approximate-inverse loss on residual probes r_t
+ *   sum_t |alpha_t (H - z) P r_t - r_t|^2 / |r_t|^2,
+ * with alpha_t = 1 (plain) or alpha_t = <(H-z)P r_t, r_t> / |(H-z)P r_t|^2
+ * (scaled: each term is then the residual reduction of one minimal-residual
+ * step with the preconditioned operator), with Adam (beta 0.9/0.999, eps
+ * 1e-8).  Supports n_alpha <= 6. */
+typedef struct bse_mlp bse_mlp;
+
+long long bse_mlp_n_params(void);
+/* Network on the current device from packed FP32 parameters (host or device). */
+bse_status bse_mlp_create(bse_mlp** out, const float* params, long long n_params);
+void bse_mlp_destroy(bse_mlp* m);
+/* Current FP32 master parameters (host or device output). */
+bse_status bse_mlp_params(const bse_mlp* m, float* out);
+/* Network outputs o [N][34] (FP32) for the handle's system at one shift. */
+bse_status bse_mlp_outputs(bse_handle* h, bse_mlp* m, double omega, double gamma, float* out);
+/* Loss and its gradient with respect to the parameters (grad [n_params],
+ * host or device, overwritten) for one shift and n_probes <= 64 probes
+ * r [n_probes][N] (device memory); scaled selects the minimal-residual form.
+ * Costs two applications of H per probe (the handle's precision, in chunks
+ * of its max_vec). */
+bse_status bse_mlp_loss_grad(bse_handle* h, bse_mlp* m, double omega, double gamma, int n_probes,
+                             const bse_c128* r, int scaled, double* loss, float* grad);
+/* One Adam step with the given gradient (host or device). */
+bse_status bse_mlp_adam_step(bse_mlp* m, const float* grad, double lr);
+/* Harvest residual probes on each system (handles hs, start vectors bs [N]
+ * each, host or device) for the n_z shifts z -- r = b and the true residuals
+ * after 1, 2 and 4 restart cycles of unpreconditioned GMRES(30); probes with
+ * |r| <= 1e-5 |b| (converged) are skipped -- then `epochs` passes over the
+ * n_sys*n_z samples in a seeded shuffled order with one Adam step per `batch`
+ * samples.  loss_per_epoch [epochs] (host) receives the mean sample loss. */
+bse_status bse_mlp_train(bse_handle* const* hs, const bse_c128* const* bs, int n_sys, const bse_c128* z,
+                         int n_z, int epochs, int batch, double lr, int seed, int scaled, bse_mlp* m,
+                         double* loss_per_epoch);
+/* Attach (or detach with NULL) the network used by BSE_PRECOND_MLP; the caller
+ * keeps ownership and must keep it alive while GMRES runs. */
+bse_status bse_gmres_set_mlp(bse_handle* h, bse_mlp* m);
 
 /* diag(H) [Na][Nk][Nb] (FP64): E_nk - chi_aa + sum_x |u_nk(x)|^2 Wbar(x)
  * + sum_pq conj(A_p) M_{ap,aq} A_q with Wbar(x) = mean_R W(x,R); the

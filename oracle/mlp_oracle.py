@@ -174,6 +174,81 @@ def grad(params, x, diag, z, rs, es, quantize=True):
     return tot, gr
 
 
+def _outputs_grad(q16, cache, o, p, g_p, g_u, g_v):
+    """Backpropagate per-row complex gradients of (p, U, V) through assemble and the network."""
+    x_, z1, h1, z2, h2 = cache
+    gs = np.conj(g_p) * p * p
+    do = np.zeros_like(o)
+    do[:, 0] = SHIFT * np.real(gs)
+    do[:, 1] = -SHIFT * np.imag(gs)
+    do[:, 2:2 + RANK] = g_u.real
+    do[:, 2 + RANK:2 + 2 * RANK] = g_u.imag
+    do[:, 2 + 2 * RANK:2 + 3 * RANK] = g_v.real
+    do[:, 2 + 3 * RANK:2 + 4 * RANK] = g_v.imag
+    gr = {"w3": h2.T @ do, "b3": do.sum(0)}
+    dz2 = (do @ q16["w3"].T) * dsilu(z2)
+    gr["w2"] = h1.T @ dz2
+    gr["b2"] = dz2.sum(0)
+    dz1 = (dz2 @ q16["w2"].T) * dsilu(z1)
+    gr["w1"] = x_.T @ dz1
+    gr["b1"] = dz1.sum(0)
+    return gr
+
+
+def _mr_scale(y, r, scaled):
+    """alpha = <y, r>/|y|^2, the minimal-residual step along y, when scaled; else 1."""
+    if not scaled:
+        return 1.0
+    yy = np.vdot(y, y).real
+    return np.vdot(y, r) / yy if yy > 0 else 0.0
+
+
+def spai_loss(params, x, diag, z, rs, apply_h, quantize=True, scaled=False):
+    """Approximate-inverse loss on residual probes:
+    sum_t |alpha_t (H - z) P r_t - r_t|^2 / |r_t|^2  (apply_h(v) = H v), with
+    alpha_t = 1 or, when scaled, the minimal-residual scale that makes each
+    term the residual reduction of one minimal-residual step with the
+    preconditioned operator (1 - cos^2 of the angle between (H - z) P r_t and r_t)."""
+    o, _ = forward(fp16(params) if quantize else params, x)
+    p, u, v = assemble(o, diag, z)
+    tot = 0.0
+    for r in rs:
+        y = apply(p, u, v, r)
+        ay = apply_h(y) - z * y
+        q = _mr_scale(ay, r, scaled) * ay - r
+        tot += float(np.vdot(q, q).real / np.vdot(r, r).real)
+    return tot
+
+
+def spai_grad(params, x, diag, z, rs, apply_h, quantize=True, scaled=False):
+    """(loss, gradient) of spai_loss.  With q_t = alpha_t (H - z) P r_t - r_t,
+    g_t = (H - z)^H conj(alpha_t) q_t = (H - conj(z)) conj(alpha_t) q_t (H
+    Hermitian; alpha_t is stationary, so it is held fixed), w_t = 2/|r_t|^2,
+    c_t = V^H r_t / N, lambda_t = U^H g_t:
+      g_p = sum_t w_t g_t conj(r_t); g_U = sum_t w_t g_t c_t^H; g_V = sum_t w_t r_t lambda_t^H / N."""
+    q16 = fp16(params) if quantize else params
+    o, cache = forward(q16, x)
+    p, u, v = assemble(o, diag, z)
+    n = x.shape[0]
+    g_p = np.zeros(n, dtype=np.complex128)
+    g_u = np.zeros((n, RANK), dtype=np.complex128)
+    g_v = np.zeros((n, RANK), dtype=np.complex128)
+    tot = 0.0
+    for r in rs:
+        c = v.conj().T @ r / n
+        y = p * r + u @ c
+        ay = apply_h(y) - z * y
+        al = _mr_scale(ay, r, scaled)
+        q = al * ay - r
+        g = np.conj(al) * (apply_h(q) - np.conj(z) * q)
+        w = 2.0 / np.vdot(r, r).real
+        tot += 0.5 * w * np.vdot(q, q).real
+        g_p += w * g * np.conj(r)
+        g_u += w * np.outer(g, np.conj(c))
+        g_v += w * np.outer(r, np.conj(u.conj().T @ g)) / n
+    return tot, _outputs_grad(q16, cache, o, p, g_p, g_u, g_v)
+
+
 def adam(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam step (t counts from 1); returns new (params, m, v)."""
     newp, newm, newv = {}, {}, {}

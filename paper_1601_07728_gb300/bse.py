@@ -18,12 +18,15 @@ LIB_PATH = os.path.join(HERE, "libbse.so")
 BSE_OK, BSE_ERR_INVALID_ARG, BSE_ERR_OOM, BSE_ERR_CUDA, BSE_ERR_BREAKDOWN, BSE_ERR_NOT_CONVERGED, \
     BSE_ERR_TIMEOUT, BSE_ERR_NAN, BSE_ERR_UNSUPPORTED = range(9)
 PREC = {"fp64": 0, "fp32": 1, "split_bf16": 2}
-PRECOND = {"none": 0, "jacobi": 1}
+PRECOND = {"none": 0, "jacobi": 1, "mlp": 2}
+GMRES_X0 = 0x100
 
 # every function declared in include/bse.h
 EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", "bse_cf_spectrum",
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
-           "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc"]
+           "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc",
+           "bse_mlp_n_params", "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_params", "bse_mlp_outputs",
+           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch"]
 KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
 
 
@@ -89,6 +92,27 @@ def lib():
     L.bse_kernel_name.restype = ctypes.c_char_p
     L.bse_short_range_noalloc.argtypes = [vp, vp, vp, vp, ci, ci, ci, ci, vp]
     L.bse_short_range_noalloc.restype = ci
+    L.bse_mlp_n_params.argtypes = []
+    L.bse_mlp_n_params.restype = cll
+    L.bse_mlp_create.argtypes = [ctypes.POINTER(vp), vp, cll]
+    L.bse_mlp_create.restype = ci
+    L.bse_mlp_destroy.argtypes = [vp]
+    L.bse_mlp_destroy.restype = None
+    L.bse_mlp_params.argtypes = [vp, vp]
+    L.bse_mlp_params.restype = ci
+    L.bse_mlp_outputs.argtypes = [vp, vp, cd, cd, vp]
+    L.bse_mlp_outputs.restype = ci
+    L.bse_mlp_loss_grad.argtypes = [vp, vp, cd, cd, ci, vp, ci, ctypes.POINTER(cd), vp]
+    L.bse_mlp_loss_grad.restype = ci
+    L.bse_mlp_adam_step.argtypes = [vp, vp, cd]
+    L.bse_mlp_adam_step.restype = ci
+    L.bse_mlp_train.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ci, vp, ci, ci, ci, cd, ci, ci, vp, vp]
+    L.bse_mlp_train.restype = ci
+    L.bse_gmres_set_mlp.argtypes = [vp, vp]
+    L.bse_gmres_set_mlp.restype = ci
+    L.bse_haydock_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ci, ci, ci, ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.bse_haydock_batch.restype = ci
     _LIB = L
     return L
 
@@ -242,6 +266,98 @@ def cf_spectrum(a, bcoef, steps, omega, gamma, terminator=False):
     if st != BSE_OK:
         raise BSEError(st, "cf_spectrum failed")
     return sig
+
+
+class MLP:
+    """The learned GMRES preconditioner network (wraps a bse_mlp)."""
+
+    def __init__(self, params):
+        L = lib()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        h = ctypes.c_void_p()
+        st = L.bse_mlp_create(ctypes.byref(h), p.ctypes.data, p.size)
+        if st != BSE_OK:
+            raise BSEError(st, "bse_mlp_create failed")
+        self.h = h
+        self.n = int(L.bse_mlp_n_params())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bse_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(self.n, dtype=np.float32)
+        _chk(lib().bse_mlp_params(self.h, out.ctypes.data))
+        return out
+
+    def outputs(self, sysg, omega, gamma):
+        out = np.empty((sysg.dim, 34), dtype=np.float32)
+        sysg._check(lib().bse_mlp_outputs(sysg.h, self.h, float(omega), float(gamma), out.ctypes.data))
+        return out
+
+    def loss_grad(self, sysg, omega, gamma, r, scaled=True):
+        """(loss, grad [n]) of the approximate-inverse loss on the device probe array r [T][N]."""
+        g = np.empty(self.n, dtype=np.float32)
+        loss = ctypes.c_double()
+        sysg._check(lib().bse_mlp_loss_grad(sysg.h, self.h, float(omega), float(gamma), r.shape[0], _ptr(r),
+                                            int(bool(scaled)), ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def adam_step(self, grad, lr):
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        _chk(lib().bse_mlp_adam_step(self.h, g.ctypes.data, float(lr)))
+
+    def train(self, systems, bs, z, epochs, batch, lr, seed=0, scaled=True):
+        """Harvest residual probes on each System and train; returns the mean loss per epoch."""
+        n = len(systems)
+        hs = (ctypes.c_void_p * n)(*[s.h.value for s in systems])
+        keep = [np.ascontiguousarray(b, dtype=np.complex128) for b in bs]
+        bp = (ctypes.c_void_p * n)(*[k.ctypes.data for k in keep])
+        zz = np.ascontiguousarray(np.atleast_1d(z), dtype=np.complex128)
+        hist = np.zeros(epochs)
+        st = lib().bse_mlp_train(hs, bp, n, zz.ctypes.data, zz.size, int(epochs), int(batch), float(lr), int(seed),
+                                 int(bool(scaled)), self.h, hist.ctypes.data)
+        if st != BSE_OK:
+            raise BSEError(st, lib().bse_last_error(systems[0].h).decode())
+        return hist
+
+
+def haydock_batch(systems, bs, n_steps, outs=None):
+    """bse_haydock_batch over Systems (each on its own stream); bs[s] [n_vec][N].
+    Returns per site (a, bcoef, steps) and the per-site statuses."""
+    n = len(systems)
+    n_vec = 1 if bs[0].ndim == 1 else bs[0].shape[0]
+    if outs is None:
+        outs = [(np.zeros((n_vec, n_steps)), np.zeros((n_vec, n_steps + 1)), np.zeros(n_vec, dtype=np.int32))
+                for _ in range(n)]
+    V = ctypes.c_void_p
+    hs = (V * n)(*[s.h.value for s in systems])
+    bp = (V * n)(*[_ptr(b) for b in bs])
+    ap = (V * n)(*[_ptr(o[0]) for o in outs])
+    bcp = (V * n)(*[_ptr(o[1]) for o in outs])
+    sp = (V * n)(*[_ptr(o[2]) for o in outs])
+    sts = np.zeros(n, dtype=np.int32)
+    st = lib().bse_haydock_batch(hs, bp, n, n_vec, int(n_steps), ap, bcp, sp, sts.ctypes.data)
+    if st not in (BSE_OK, BSE_ERR_BREAKDOWN):
+        raise BSEError(st, "bse_haydock_batch")
+    return outs, sts
+
+
+def _chk(st):
+    if st != BSE_OK:
+        raise BSEError(st)
+    return st
+
+
+def attach_mlp(sysg, mlp):
+    sysg._check(lib().bse_gmres_set_mlp(sysg.h, mlp.h if mlp is not None else None))
 
 
 def short_range_noalloc(a_proj, m_sr, psi, out, n_alpha, stream=None):

@@ -86,6 +86,7 @@ void free_handle(bse_handle* h) {
   if (h->io_in) cudaFree(h->io_in);
   if (h->io_out) cudaFree(h->io_out);
   if (h->ws) cudaFree(h->ws);
+  if (h->mlp_anorm) cudaFree(h->mlp_anorm);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -254,6 +255,42 @@ bse_status bse_haydock(bse_handle* h, const bse_c128* b, int n_vec, int n_steps,
   return s;
 }
 
+bse_status bse_haydock_batch(bse_handle* const* hs, const bse_c128* const* b, int n_sites, int n_vec, int n_steps,
+                             double* const* a, double* const* bcoef, int* const* steps_done, int* site_status) {
+  if (!hs || !b || !a || !bcoef || !steps_done || !site_status || n_sites < 1 || n_vec < 1 || n_steps < 1)
+    return BSE_ERR_INVALID_ARG;
+  for (int s = 0; s < n_sites; ++s)
+    if (!hs[s] || !b[s] || !a[s] || !bcoef[s] || !steps_done[s]) return BSE_ERR_INVALID_ARG;
+  std::vector<Staged> sb(n_sites), sa(n_sites), sbb(n_sites), ss(n_sites);
+  std::vector<const double2*> bd(n_sites);
+  std::vector<double*> ad(n_sites), bcd(n_sites);
+  std::vector<int*> sd(n_sites);
+  for (int s = 0; s < n_sites; ++s) {
+    bse_handle* h = hs[s];
+    TRY(stage_in(h, sb[s], b[s], (size_t)n_vec * h->N * sizeof(double2), true, "b"));
+    TRY(stage_in(h, sa[s], a[s], (size_t)n_vec * n_steps * sizeof(double), false, "a"));
+    TRY(stage_in(h, sbb[s], bcoef[s], (size_t)n_vec * (n_steps + 1) * sizeof(double), false, "bcoef"));
+    TRY(stage_in(h, ss[s], steps_done[s], (size_t)n_vec * sizeof(int), false, "steps_done"));
+    TRY(bse_cuda_check(h, cudaStreamSynchronize(h->stream), "batch staging"));
+    bd[s] = (const double2*)sb[s].dev;
+    ad[s] = (double*)sa[s].dev;
+    bcd[s] = (double*)sbb[s].dev;
+    sd[s] = (int*)ss[s].dev;
+  }
+  std::vector<bse_status> st(n_sites, BSE_OK);
+  bse_status worst = bse_haydock_batch_device(hs, bd.data(), n_sites, n_vec, n_steps, ad.data(), bcd.data(),
+                                              sd.data(), st.data());
+  for (int s = 0; s < n_sites; ++s) {
+    bse_handle* h = hs[s];
+    site_status[s] = st[s];
+    TRY(stage_out(h, sa[s], a[s], (size_t)n_vec * n_steps * sizeof(double), "a copy-out"));
+    TRY(stage_out(h, sbb[s], bcoef[s], (size_t)n_vec * (n_steps + 1) * sizeof(double), "b copy-out"));
+    TRY(stage_out(h, ss[s], steps_done[s], (size_t)n_vec * sizeof(int), "steps copy-out"));
+    TRY(bse_cuda_check(h, cudaStreamSynchronize(h->stream), "batch sync"));
+  }
+  return worst;
+}
+
 bse_status bse_cf_spectrum(const double* a, const double* bcoef, const int* steps, int n_vec, int n_stride,
                            const double* omega, int n_omega, double gamma, int terminator, double* sigma) {
   if (!a || !bcoef || !steps || !omega || !sigma || n_vec < 1 || n_stride < 1 || n_omega < 0)
@@ -280,7 +317,8 @@ bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_
   if (!b || !z || !x || !iters || !rel_resid || n_z < 1 || restart < 1 || max_iter < 1 || !(rtol > 0))
     return bse_fail(h, BSE_ERR_INVALID_ARG, "gmres: bad arguments");
   const int pkind = precond & 0xff;
-  if ((precond & ~(0xff | BSE_GMRES_X0)) != 0 || (pkind != BSE_PRECOND_NONE && pkind != BSE_PRECOND_JACOBI))
+  if ((precond & ~(0xff | BSE_GMRES_X0)) != 0 ||
+      (pkind != BSE_PRECOND_NONE && pkind != BSE_PRECOND_JACOBI && pkind != BSE_PRECOND_MLP))
     return bse_fail(h, BSE_ERR_INVALID_ARG, "gmres: unknown preconditioner");
   Staged sb, sz, sx, si, sr;
   TRY(stage_in(h, sb, b, (size_t)h->N * sizeof(double2), true, "b"));
@@ -297,6 +335,13 @@ bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_
   TRY(bse_cuda_check(h, cudaStreamSynchronize(h->stream), "gmres sync"));
   TRY(bse_tc_status(h));
   return s;
+}
+
+bse_status bse_gmres_set_mlp(bse_handle* h, bse_mlp* m) {
+  if (!h) return BSE_ERR_INVALID_ARG;
+  if (m && h->na > 6) return bse_fail(h, BSE_ERR_UNSUPPORTED, "learned preconditioner supports up to 6 core states");
+  h->mlp = m;
+  return BSE_OK;
 }
 
 const char* bse_kernel_name(int kind) {

@@ -80,6 +80,11 @@ struct bse_handle {
   void* tmap = nullptr;             // SPLIT_BF16: tensor maps (device copy)
   void* tmap_host = nullptr;
 
+  // learned GMRES preconditioner attached by the caller (not owned), and the
+  // per-(k,n) local-basis weight |A_{:,nk}| it uses as a feature
+  bse_mlp* mlp = nullptr;
+  float* mlp_anorm = nullptr;
+
   // side stream for the short-range term (overlaps the band->grid pass)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -163,6 +168,9 @@ void bse_tc_free(bse_handle* h);
 // Krylov drivers (k_krylov.cu)
 bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_steps, int reorth,
                               double* a, double* bcoef, int* steps_done);
+bse_status bse_haydock_batch_device(bse_handle* const* hs, const double2* const* bs, int n_sites, int n_vec,
+                                    int n_steps, double* const* a_d, double* const* b_d, int* const* steps_d,
+                                    bse_status* site_status);
 bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, int n_z, double rtol,
                             int restart, int max_iter, int precond, double2* x, int* iters,
                             double* rel_resid);

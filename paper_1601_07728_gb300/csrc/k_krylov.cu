@@ -558,6 +558,10 @@ __global__ void gm_update_x(const double2* __restrict__ V, long long vstride, co
       acc.x += c.x * a.x - c.y * a.y;
       acc.y += c.x * a.y + c.y * a.x;
     }
+    if (jacobi == 2) {   // learned preconditioner: keep V y, P is applied afterwards
+      x[(size_t)v * N + e] = acc;
+      continue;
+    }
     if (jacobi) acc = cdiv(acc, make_double2(d[e] - zv.x, -zv.y));
     double2 o = x[(size_t)v * N + e];
     x[(size_t)v * N + e] = make_double2(o.x + acc.x, o.y + acc.y);
@@ -565,6 +569,13 @@ __global__ void gm_update_x(const double2* __restrict__ V, long long vstride, co
 }
 
 }  // namespace
+
+// learned preconditioner (k_mlp.cu)
+bse_status bse_mlp_factors(bse_handle* h, bse_mlp* m, const double2* z_host, int n_z, float2* p, float2* u, float2* v);
+bse_status bse_mlp_apply(bse_handle* h, const float2* p, const float2* u, const float2* v, const double2* x,
+                         long long xstride, int ns, const int* idx, double2* y, long long ystride, int add,
+                         double2* part, long long fstride);
+size_t bse_mlp_apply_scratch(int ns);
 
 // ---------------------------------------------------------------------------
 namespace {
@@ -626,27 +637,40 @@ __global__ void __launch_bounds__(RB) hay_update_fin(double2* __restrict__ w, co
 }
 }  // namespace
 
-bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_steps, int reorth,
-                              double* a_d, double* b_d, int* steps_d) {
+namespace {
+// Grow-only Haydock workspace of a handle: three vectors, partial sums, flags.
+size_t hay_ws_bytes(long long N, int n_vec) {
+  return 3 * (size_t)n_vec * N * sizeof(double2) + (size_t)n_vec * NBLK * sizeof(double2) +
+         (size_t)n_vec * BSE_FINAL_BLOCKS * sizeof(double2) + 256 + (size_t)n_vec * sizeof(int) + 256;
+}
+
+bse_status hay_reserve(bse_handle* h, int n_vec) {
+  const size_t need = hay_ws_bytes(h->N, n_vec);
+  if (h->ws_cap >= need) return BSE_OK;
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_cap = 0;
+  TRY(dalloc(h, (char**)&h->ws, need, "haydock workspace"));
+  h->ws_cap = need;
+  return BSE_OK;
+}
+
+// Enqueue one Haydock run on the handle's stream (no host synchronisation).
+// Buffers that must outlive the launches are registered in `fr`; the device
+// status word is returned through status_out.  With allow_graph the step loop
+// is captured into a CUDA graph of its own.
+bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, int reorth, double* a_d,
+                       double* b_d, int* steps_d, Freer& fr, int** status_out, bool allow_graph) {
   cudaStream_t st = h->stream;
   const long long N = h->N;
-  Freer fr;
   double2 *v3 = nullptr, *partial = nullptr, *basis = nullptr, *coef = nullptr, *fpart = nullptr;
   int *active = nullptr, *status = nullptr;
   unsigned* counters = nullptr;
   {
-    // three vectors, partial sums, flags: one grow-only workspace kept by the handle
+    TRY(hay_reserve(h, n_vec));
     const size_t bv = 3 * (size_t)n_vec * N * sizeof(double2);
     const size_t bp = (size_t)n_vec * NBLK * sizeof(double2);
     const size_t bf = (size_t)n_vec * BSE_FINAL_BLOCKS * sizeof(double2);
-    const size_t need = bv + bp + bf + 256 + (size_t)n_vec * sizeof(int) + 256;
-    if (h->ws_cap < need) {
-      if (h->ws) cudaFree(h->ws);
-      h->ws = nullptr;
-      h->ws_cap = 0;
-      TRY(dalloc(h, (char**)&h->ws, need, "haydock workspace"));
-      h->ws_cap = need;
-    }
     char* p = (char*)h->ws;
     v3 = (double2*)p;
     partial = (double2*)(p + bv);
@@ -686,7 +710,7 @@ bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_
   // gaps between the ~10 kernels of a step otherwise cost ~8 % of the step);
   // without a capturable stream, or with per-launch profiling on, it runs
   // eagerly.
-  const bool want_graph = !h->prof && h->stream != nullptr && !getenv("BSE_NO_GRAPH");
+  const bool want_graph = allow_graph && !h->prof && h->stream != nullptr && !getenv("BSE_NO_GRAPH");
   bool capturing = false;
   if (want_graph) {
     capturing = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -753,14 +777,91 @@ bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_
   if (ge == cudaSuccess && loop_status == BSE_OK) break;
   cudaGetLastError();   // capture refused: run the same launches eagerly
   }
+  *status_out = status;
   TRY(loop_status);
-  TRY(bse_cuda_check(h, cudaGetLastError(), "haydock kernels"));
+  return bse_cuda_check(h, cudaGetLastError(), "haydock kernels");
+}
+
+// wait for the run and map its device status word
+bse_status hay_finish(bse_handle* h, const int* status) {
   int hs = 0;
-  TRY(bse_cuda_check(h, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st), "status copy"));
-  TRY(bse_cuda_check(h, cudaStreamSynchronize(st), "haydock sync"));
+  TRY(bse_cuda_check(h, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status copy"));
+  TRY(bse_cuda_check(h, cudaStreamSynchronize(h->stream), "haydock sync"));
   if (hs & ST_NAN) return bse_fail(h, BSE_ERR_NAN, "non-finite Haydock coefficient");
   if (hs & ST_BREAKDOWN) return BSE_ERR_BREAKDOWN;
   return BSE_OK;
+}
+}  // namespace
+
+bse_status bse_haydock_device(bse_handle* h, const double2* b, int n_vec, int n_steps, int reorth, double* a_d,
+                              double* b_d, int* steps_d) {
+  Freer fr;
+  int* status = nullptr;
+  TRY(hay_enqueue(h, b, n_vec, n_steps, reorth, a_d, b_d, steps_d, fr, &status, true));
+  return hay_finish(h, status);
+}
+
+// Several sites (one handle each, each on its own stream) recorded into ONE
+// CUDA graph: a master stream forks to every site stream, each site's whole
+// Haydock run is captured there, and the streams join back.  One graph launch
+// then runs every site, the kernels of different sites overlapping on the GPU.
+// Falls back to one site after another when a stream cannot be captured.
+bse_status bse_haydock_batch_device(bse_handle* const* hs, const double2* const* bs, int n_sites, int n_vec,
+                                    int n_steps, double* const* a_d, double* const* b_d, int* const* steps_d,
+                                    bse_status* site_status) {
+  std::vector<Freer> frs(n_sites);
+  std::vector<int*> status(n_sites, nullptr);
+  bool capturable = true;
+  for (int s = 0; s < n_sites; ++s) capturable = capturable && hs[s]->stream != nullptr && !hs[s]->prof;
+  for (int s = 0; s < n_sites && capturable; ++s)
+    for (int t = s + 1; t < n_sites; ++t) capturable = capturable && hs[s]->stream != hs[t]->stream;
+  for (int s = 0; s < n_sites; ++s) TRY(hay_reserve(hs[s], n_vec));   // no allocation while capturing
+  cudaStream_t master = nullptr;
+  std::vector<cudaEvent_t> ev(n_sites + 1, nullptr);
+  bool graph_done = false;
+  if (capturable && !getenv("BSE_NO_GRAPH") && cudaStreamCreateWithFlags(&master, cudaStreamNonBlocking) == cudaSuccess) {
+    bool ok = true;
+    for (auto& e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaEventRecord(ev[n_sites], master);
+      bse_status es = BSE_OK;
+      for (int s = 0; s < n_sites && es == BSE_OK; ++s) {
+        cudaStreamWaitEvent(hs[s]->stream, ev[n_sites], 0);
+        es = hay_enqueue(hs[s], bs[s], n_vec, n_steps, 0, a_d[s], b_d[s], steps_d[s], frs[s], &status[s], false);
+        cudaEventRecord(ev[s], hs[s]->stream);
+        cudaStreamWaitEvent(master, ev[s], 0);
+      }
+      cudaGraph_t graph = nullptr;
+      cudaError_t ge = cudaStreamEndCapture(master, &graph);
+      cudaGraphExec_t exec = nullptr;
+      if (ge == cudaSuccess && es == BSE_OK) ge = cudaGraphInstantiate(&exec, graph, 0);
+      if (ge == cudaSuccess && es == BSE_OK) ge = cudaGraphLaunch(exec, master);
+      if (ge == cudaSuccess && es == BSE_OK) ge = cudaStreamSynchronize(master);
+      graph_done = ge == cudaSuccess && es == BSE_OK;
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (master) cudaStreamDestroy(master);
+  if (!graph_done) {   // one site after another, each with its own captured loop
+    for (int s = 0; s < n_sites; ++s) {
+      site_status[s] = hay_enqueue(hs[s], bs[s], n_vec, n_steps, 0, a_d[s], b_d[s], steps_d[s], frs[s], &status[s],
+                                   true);
+    }
+  }
+  bse_status worst = BSE_OK;
+  for (int s = 0; s < n_sites; ++s) {
+    if (!graph_done && site_status[s] != BSE_OK) {
+      worst = site_status[s];
+      continue;
+    }
+    site_status[s] = hay_finish(hs[s], status[s]);
+    if (site_status[s] != BSE_OK && site_status[s] != BSE_ERR_BREAKDOWN) worst = site_status[s];
+  }
+  return worst;
 }
 
 bse_status bse_cf_device(const double* a, const double* bcoef, const int* steps, int n_vec, int n_stride,
@@ -778,6 +879,23 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
   const long long N = h->N;
   const int m = restart;
   const int jac = (precond & 0xff) == BSE_PRECOND_JACOBI;
+  const bool mlp = (precond & 0xff) == BSE_PRECOND_MLP;
+  if (mlp && !h->mlp) return bse_fail(h, BSE_ERR_INVALID_ARG, "gmres: no preconditioner network attached");
+  float2 *pc_p = nullptr, *pc_u = nullptr, *pc_v = nullptr;
+  double2* pc_part = nullptr;
+  Freer frm;
+  if (mlp) {
+    // per-shift factors of P = diag(p) + U V^H / N from the network (one forward pass per shift)
+    std::vector<double2> zh(n_z);
+    TRY(bse_cuda_check(h, cudaMemcpyAsync(zh.data(), z, n_z * sizeof(double2), cudaMemcpyDefault, h->stream), "z copy"));
+    TRY(bse_cuda_check(h, cudaStreamSynchronize(h->stream), "z sync"));
+    const size_t n = (size_t)h->N;
+    TRY(dalloc(h, &pc_p, (size_t)n_z * n * sizeof(float2), "precond p")); frm.add(pc_p);
+    TRY(dalloc(h, &pc_u, (size_t)n_z * n * 8 * sizeof(float2), "precond U")); frm.add(pc_u);
+    TRY(dalloc(h, &pc_v, (size_t)n_z * n * 8 * sizeof(float2), "precond V")); frm.add(pc_v);
+    TRY(dalloc(h, &pc_part, bse_mlp_apply_scratch(n_z), "precond scratch")); frm.add(pc_part);
+    TRY(bse_mlp_factors(h, h->mlp, zh.data(), n_z, pc_p, pc_u, pc_v));
+  }
   Freer fr;
   double2 *V, *T, *W, *partial, *Hs, *sn, *g, *y, *coef;
   double *cs, *beta, *hnorm, *est;
@@ -845,7 +963,11 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
         if (hact[v]) hidx[ns++] = v;
       TRY(bse_cuda_check(h, cudaMemcpyAsync(didx, hidx.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st), "idx"));
       const dim3 ec(eg.x, (unsigned)ns);
-      BSE_PROF(h, BSE_K_RECURSION, gm_precond_c<<<ec, 256, 0, st>>>(V + (size_t)j * N, vstride, T, N, h->jdiag, z, jac, didx));
+      if (mlp) {
+        TRY(bse_mlp_apply(h, pc_p, pc_u, pc_v, V + (size_t)j * N, vstride, ns, didx, T, N, 0, pc_part, 1));
+      } else {
+        BSE_PROF(h, BSE_K_RECURSION, gm_precond_c<<<ec, 256, 0, st>>>(V + (size_t)j * N, vstride, T, N, h->jdiag, z, jac, didx));
+      }
       TRY(apply_chunked(h, T, Wc, ns));
       BSE_PROF(h, BSE_K_RECURSION, gm_scatter_shift<<<ec, 256, 0, st>>>(Wc, T, z, W, N, didx));
       TRY(cgs2(h, V, vstride, W, n_z, j + 1, partial, coef, m + 1, Hs + (size_t)j * (m + 1),
@@ -863,7 +985,14 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
       if (nact == 0) break;
     }
     BSE_PROF(h, BSE_K_RECURSION, gm_solve<<<(n_z + 127) / 128, 128, 0, st>>>(Hs, g, y, jdone, m, n_z));
-    BSE_PROF(h, BSE_K_RECURSION, gm_update_x<<<eg, 256, 0, st>>>(V, vstride, y, jdone, m, x, N, h->jdiag, z, jac));
+    if (mlp) {
+      // x += P (V y): V y into W (zero for systems without new columns), then P
+      cudaMemsetAsync(W, 0, (size_t)n_z * N * sizeof(double2), st);
+      BSE_PROF(h, BSE_K_RECURSION, gm_update_x<<<eg, 256, 0, st>>>(V, vstride, y, jdone, m, W, N, h->jdiag, z, 2));
+      TRY(bse_mlp_apply(h, pc_p, pc_u, pc_v, W, N, n_z, nullptr, x, N, 1, pc_part, 1));
+    } else {
+      BSE_PROF(h, BSE_K_RECURSION, gm_update_x<<<eg, 256, 0, st>>>(V, vstride, y, jdone, m, x, N, h->jdiag, z, jac));
+    }
   }
   TRY(bse_cuda_check(h, cudaGetLastError(), "gmres kernels"));
   std::vector<int> hit(n_z);

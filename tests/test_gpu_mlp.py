@@ -1,0 +1,144 @@
+"""GPU kernels of the learned GMRES preconditioner against the FP64 oracle
+(oracle/mlp_oracle.py): network outputs, loss gradient, Adam, and GMRES with
+the preconditioner attached.
+
+Tolerances: outputs and gradients are computed with FP16 weights and FP32
+accumulation on the GPU versus FP64 arithmetic on the same FP16-rounded
+weights in the oracle: 2e-4 relative for outputs, 5e-3 relative (L2 per
+parameter block) for gradients, whose probe reductions run over N terms in
+FP32 products (the H applications and probe statistics are FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import bse_oracle as O
+from oracle import mlp_oracle as M
+from paper_1601_07728_gb300 import bse, synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    a = a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = S.tiny_system(62, n_alpha=6, nk=(2, 2, 2), n_bands=10, nx=(4, 4, 4), n_proj=4)
+    rng = np.random.default_rng(11)
+    params = S.mlp_init(5).astype(np.float64)
+    pr = M.unpack(params)
+    pr["w3"] = pr["w3"] + 0.05 * rng.standard_normal(pr["w3"].shape)
+    pr["b3"] = 0.05 * rng.standard_normal(pr["b3"].shape)
+    flat = M.pack(M.fp16(pr)).astype(np.float32)
+    return s, flat
+
+
+def test_outputs_match_oracle(tiny):
+    s, flat = tiny
+    sysg = bse.System(s, precision="fp64")
+    net = bse.MLP(flat)
+    diag = O.jacobi_diag(s).reshape(-1)
+    for om in (-2.0, 6.5):
+        out = net.outputs(sysg, om, 0.5)
+        ref, _ = M.forward(M.fp16(M.unpack(flat.astype(np.float64))), M.system_features(s, diag, om, 0.5))
+        assert rel(out, ref) < 2e-4
+
+
+@pytest.mark.parametrize("scaled", [False, True])
+def test_gradient_matches_oracle(tiny, scaled):
+    """Approximate-inverse loss on three probes (two FP64 applications of H
+    per probe on the GPU) and its gradient against the oracle's."""
+    torch = pytest.importorskip("torch")
+    s, flat = tiny
+    sysg = bse.System(s, precision="fp64", max_vec=2)
+    net = bse.MLP(flat)
+    rng = np.random.default_rng(12)
+    rs = S.complex_normal(rng, (3, s.dim))
+    om, g = 4.0, 0.5
+    loss, grad = net.loss_grad(sysg, om, g, torch.from_numpy(rs).cuda(), scaled=scaled)
+    diag = O.jacobi_diag(s).reshape(-1)
+    lo, go = M.spai_grad(M.unpack(flat.astype(np.float64)), M.system_features(s, diag, om, g), diag, om + 1j * g,
+                         list(rs), lambda v: O.apply_h(s, v), scaled=scaled)
+    assert loss == pytest.approx(lo, rel=1e-4)
+    gg = M.unpack(grad.astype(np.float64))
+    for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        assert rel(gg[name], go[name]) < 5e-3, name
+
+
+def test_adam_step_matches_oracle(tiny):
+    s, flat = tiny
+    net = bse.MLP(flat)
+    rng = np.random.default_rng(13)
+    grad = (rng.standard_normal(flat.size) * 0.1).astype(np.float32)
+    net.adam_step(grad, 1e-3)
+    net.adam_step(0.5 * grad, 1e-3)
+    p = M.unpack(flat.astype(np.float64))
+    z = {k: np.zeros_like(v) for k, v in p.items()}
+    p1, m1, v1 = M.adam(p, M.unpack(grad.astype(np.float64)), z, z, 1, 1e-3)
+    p2, _, _ = M.adam(p1, M.unpack(0.5 * grad.astype(np.float64)), m1, v1, 2, 1e-3)
+    assert rel(net.params(), M.pack(p2)) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def reduced():
+    s = S.reduced_l23(0)
+    return s, S.make_start_vectors(s, 1)[0]
+
+
+TRAIN_Z = np.linspace(-3.0, 25.0, 8) + 0.5j
+HELD_OUT_Z = np.array([2.0, 10.8, 17.8]) + 0.5j
+
+
+@pytest.fixture(scope="module")
+def trained(reduced):
+    """Network trained on the GPU (probe harvest by GMRES, loss and gradient
+    by the library's kernels, Adam) at eight shifts of the reduced L2,3 system."""
+    s, b = reduced
+    sysg = bse.System(s, precision="fp64", max_vec=4)
+    net = bse.MLP(S.mlp_init(0))
+    hist = net.train([sysg], [b], TRAIN_Z, epochs=10, batch=1, lr=1e-3, seed=1, scaled=True)
+    return net, hist
+
+
+def test_training_reduces_loss(trained):
+    """The mean sample loss (minimal-residual form) falls over the epochs."""
+    net, hist = trained
+    assert np.all(np.isfinite(hist))
+    assert hist[-1] < 0.95 * hist[0]
+
+
+def test_trained_network_beats_no_preconditioner(reduced, trained):
+    """Gain of the trained network at shifts it was not trained on: GMRES(30)
+    reaches the same solution (true residual 1e-8) in fewer iterations than
+    GMRES without a preconditioner."""
+    s, b = reduced
+    net, _ = trained
+    sysg = bse.System(s, precision="fp64", max_vec=3)
+    bse.attach_mlp(sysg, net)
+    x0, it0, r0, st0 = sysg.gmres(b, HELD_OUT_Z, rtol=1e-8, restart=30, max_iter=3000, precond="none")
+    x1, it1, r1, st1 = sysg.gmres(b, HELD_OUT_Z, rtol=1e-8, restart=30, max_iter=3000, precond="mlp")
+    assert st0 == bse.BSE_OK and st1 == bse.BSE_OK
+    for j in range(len(HELD_OUT_Z)):
+        assert rel(x1[j], x0[j]) < 1e-6
+    assert np.all(r1 <= 1e-8)
+    assert np.all(it1 < it0), (it0, it1)
+
+
+def test_gmres_with_prior_network(reduced):
+    """The untrained network (last layer zero) is the damped diagonal
+    1/(D - omega - i(Gamma + 4.5 eV)): GMRES converges to the same solution in
+    fewer iterations than without preconditioning."""
+    s, b = reduced
+    sysg = bse.System(s, precision="fp64", max_vec=3)
+    net = bse.MLP(S.mlp_init(0))
+    bse.attach_mlp(sysg, net)
+    z = HELD_OUT_Z
+    x0, it0, r0, st0 = sysg.gmres(b, z, rtol=1e-8, restart=30, max_iter=3000, precond="none")
+    x1, it1, r1, st1 = sysg.gmres(b, z, rtol=1e-8, restart=30, max_iter=3000, precond="mlp")
+    assert st0 == bse.BSE_OK and st1 == bse.BSE_OK
+    for j in range(3):
+        assert rel(x1[j], x0[j]) < 1e-6
+    assert np.all(it1 < it0)

@@ -50,6 +50,49 @@ def test_gradient_matches_central_differences(problem):
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, idx, fd, an)
 
 
+@pytest.mark.parametrize("scaled", [False, True])
+def test_spai_gradient_matches_central_differences(problem, scaled):
+    """Approximate-inverse loss sum_t |alpha_t (H - z) P r_t - r_t|^2/|r_t|^2 on
+    residual probes (alpha_t = 1, or the minimal-residual scale):
+    backpropagation (through two H applications per probe) against central
+    differences of the FP64 network."""
+    s, diag, z, x, rs, es, params = problem
+    p16 = M.fp16(params)
+    happly = lambda v: O.apply_h(s, v)
+    tot, g = M.spai_grad(p16, x, diag, z, rs, happly, scaled=scaled)
+    assert tot == pytest.approx(M.spai_loss(p16, x, diag, z, rs, happly, scaled=scaled), rel=1e-12)
+    rng = np.random.default_rng(9)
+    h = 1e-6
+    for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        flat = p16[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=3, replace=False):
+            up = {k: v.copy() for k, v in p16.items()}
+            dn = {k: v.copy() for k, v in p16.items()}
+            up[name].reshape(-1)[idx] += h
+            dn[name].reshape(-1)[idx] -= h
+            fd = (M.spai_loss(up, x, diag, z, rs, happly, quantize=False, scaled=scaled)
+                  - M.spai_loss(dn, x, diag, z, rs, happly, quantize=False, scaled=scaled)) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, idx, fd, an)
+
+
+def test_spai_optimal_diagonal_closed_form():
+    """For a diagonal P the approximate-inverse loss over all unit probes is
+    |A diag(p) - I|_F^2, minimised column by column by
+    p_j = conj(A_jj) / |A_:j|^2 -- the damped diagonal the network starts from
+    approximates exactly this."""
+    s = S.tiny_system(63, n_alpha=2, nk=(2, 1, 1), n_bands=3, nx=(2, 2, 2), n_proj=2)
+    h = O.dense_h(s)
+    z = 3.0 + 0.5j
+    a = h - z * np.eye(s.dim)
+    p_opt = np.conj(np.diag(a)) / (np.abs(a) ** 2).sum(0)
+    f = lambda p: np.linalg.norm(a @ np.diag(p) - np.eye(s.dim)) ** 2
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        dp = 1e-3 * (rng.standard_normal(s.dim) + 1j * rng.standard_normal(s.dim))
+        assert f(p_opt + dp) > f(p_opt)
+
+
 def test_zero_network_is_damped_diagonal(problem):
     """Last layer zero: P = diag(1 / (D - omega - i(Gamma + ETA0)))."""
     s, diag, z, x, rs, es, params = problem
@@ -60,6 +103,25 @@ def test_zero_network_is_damped_diagonal(problem):
     p, u, v = M.assemble(o, diag, z)
     assert np.allclose(p, 1.0 / (diag - z.real - 1j * (z.imag + M.ETA0)), rtol=1e-14)
     assert np.abs(u).max() == 0 and np.abs(v).max() == 0
+
+
+def test_scaled_loss_is_one_step_minimal_residual(problem):
+    """The scaled per-probe term equals the squared residual reduction of one
+    minimal-residual step min_a |r - a (H - z) P r|^2 / |r|^2, found here by a
+    least-squares solve on the dense operator."""
+    s, diag, z, x, rs, es, params = problem
+    o, _ = M.forward(M.fp16(params), x)
+    p, u, v = M.assemble(o, diag, z)
+    a = O.dense_h(s) - z * np.eye(s.dim)
+    pd = np.diag(p) + u @ v.conj().T / s.dim
+    want = 0.0
+    for r in rs:
+        col = (a @ pd @ r)[:, None]
+        coef = np.linalg.lstsq(col, r, rcond=None)[0]
+        want += np.linalg.norm(r - col @ coef) ** 2 / np.linalg.norm(r) ** 2
+    got = M.spai_loss(params, x, diag, z, rs, lambda v: O.apply_h(s, v), scaled=True)
+    assert got == pytest.approx(want, rel=1e-10)
+    assert 0.0 <= got <= len(rs)
 
 
 def test_low_rank_operator_against_dense(problem):
