@@ -42,13 +42,17 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default=os.environ.get("BSE_BENCH_PRECISION", "fp32"))
+    p.add_argument("--precision", default=os.environ.get("BSE_BENCH_PRECISION", "split_bf16"))
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--gmres-omega", type=int, default=40, help="shifts in the GMRES measurement (0 = skip)")
     p.add_argument("--gmres-max-iter", type=int, default=2000)
     p.add_argument("--gmres-chunk", type=int, default=10, help="systems per batched H application")
+    p.add_argument("--gmres-fp64-omega", type=int, default=4,
+                   help="shifts (every n-th of the GMRES set) also solved by the plain FP64 form (0 = skip)")
+    p.add_argument("--train-omega", type=int, default=8, help="training shifts of the learned preconditioner")
+    p.add_argument("--train-epochs", type=int, default=10)
     return p.parse_args()
 
 
@@ -282,6 +286,20 @@ def main():
     steps_done = int(st_d.item())
     value = world * steps_done / (t_max / 1e3)
 
+    # spectrum error of this run against the FP64 oracle's stored Haydock
+    # coefficients for the same workload and start vector (both spectra
+    # evaluated by the same continued fraction on the 2000-point grid)
+    spec = None
+    gold = os.path.join(ROOT, "tests", "golden", "%s_haydock200.npz" % args.workload)
+    if os.path.exists(gold) and steps_done > 0:
+        g = np.load(gold)
+        kk = min(steps_done, int(g["steps"]))
+        om = np.linspace(-5.0, 30.0, 2000)
+        sg = bse.cf_spectrum(a_d.cpu().numpy()[:kk], b_d.cpu().numpy()[:kk + 1], kk, om, 0.5)[0]
+        so = bse.cf_spectrum(g["a"][:kk], g["b"][:kk + 1], kk, om, 0.5)[0]
+        spec = {"steps": kk, "rel_l2_vs_fp64_oracle": float(np.linalg.norm(sg - so) / np.linalg.norm(so)),
+                "grid": "2000 omega in [-5, 30] eV, Gamma 0.5 eV"}
+
     # GMRES: (H - omega - i Gamma) x = b for n_omega shifts, all advanced together
     gm = None
     if args.gmres_omega > 0:
@@ -292,13 +310,13 @@ def main():
         sys_g.gmres(db, zs[:2], rtol=1e-3, restart=30, max_iter=60, precond="none", x=xg[:2])   # warm-up
         gm = {"n_omega": n_om, "rtol": 1e-6, "restart": 30, "max_iter": args.gmres_max_iter,
               "shifts": "omega in linspace(-5, 30, %d) eV + 0.5i" % n_om, "chunk": args.gmres_chunk}
-        for pc in ("none", "jacobi"):
+        def leg(system, pc, z, x):
             torch.cuda.synchronize()
             barrier()
-            l1 = sys_g.launches
+            l1 = system.launches
             g0 = time.perf_counter()
-            _, g_it, g_rr, g_st = sys_g.gmres(db, zs, rtol=1e-6, restart=30, max_iter=args.gmres_max_iter,
-                                              precond=pc, x=xg)
+            _, g_it, g_rr, g_st = system.gmres(db, z, rtol=1e-6, restart=30, max_iter=args.gmres_max_iter,
+                                               precond=pc, x=x)
             torch.cuda.synchronize()
             g_el = time.perf_counter() - g0
             if dist is not None:
@@ -306,9 +324,50 @@ def main():
                 dist.all_reduce(t, op=dist.ReduceOp.MAX)
                 g_el = float(t.item())
             conv = int(np.sum(g_rr <= 1e-6))
-            gm[pc] = {"solves_per_s": world * conv / g_el, "seconds": g_el, "converged": conv,
-                      "iters_mean": float(np.mean(g_it)), "iters_max": int(np.max(g_it)),
-                      "max_rel_resid": float(np.max(g_rr)), "gpu_launches": sys_g.launches - l1}
+            return {"solves_per_s": world * conv / g_el, "seconds": g_el, "converged": conv, "n_omega": len(z),
+                    "iters_mean": float(np.mean(g_it)), "iters_max": int(np.max(g_it)),
+                    "max_rel_resid": float(np.max(g_rr)), "gpu_launches": system.launches - l1}
+
+        def sigma_of(x):
+            # sigma(omega) = (1/pi) Im <b|x(z)>
+            return (torch.imag(x @ db.conj()) / np.pi).cpu().numpy()
+
+        gm["none"] = leg(sys_g, "none", zs, xg)
+        sig_none = sigma_of(xg)
+        gm["jacobi"] = leg(sys_g, "jacobi", zs, xg)
+        # learned preconditioner: the network's prior (last layer zero: the damped
+        # diagonal) and the network after training on the GPU at shifts between the
+        # measured ones (residual probes of plain GMRES(30), minimal-residual loss)
+        net = bse.MLP(S.mlp_init(0))
+        bse.attach_mlp(sys_g, net)
+        gm["mlp_prior"] = leg(sys_g, "mlp", zs, xg)
+        if args.train_omega > 0:
+            step = (zs[1].real - zs[0].real) if n_om > 1 else 1.0
+            zt = np.linspace(-5.0 + 0.5 * step, 30.0 - 0.5 * step, args.train_omega) + 0.5j
+            torch.cuda.synchronize()
+            t_tr = time.perf_counter()
+            hist = net.train([sys_g], [b], zt, epochs=args.train_epochs, batch=1, lr=1e-3, seed=1, scaled=True)
+            torch.cuda.synchronize()
+            t_tr = time.perf_counter() - t_tr
+            gm["mlp_trained"] = leg(sys_g, "mlp", zs, xg)
+            gm["mlp_trained"]["training"] = {
+                "seconds": t_tr, "shifts": args.train_omega, "epochs": args.train_epochs,
+                "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1]),
+                "note": "shifts held out from the measured set (midpoints); training timed separately"}
+        bse.attach_mlp(sys_g, None)
+        del net
+        if args.gmres_fp64_omega > 0:
+            # plain FP64 form on a subset of the shifts, and the spectrum difference
+            # sigma = Im<b|x>/pi between this form and it at those shifts
+            sel = np.linspace(0, n_om - 1, min(args.gmres_fp64_omega, n_om)).round().astype(int)
+            sys64 = bse.System(s, precision="fp64", max_vec=len(sel), stream=stream.cuda_stream)
+            x64 = torch.empty((len(sel), n), dtype=torch.complex128, device="cuda")
+            gm["fp64_none"] = leg(sys64, "none", zs[sel], x64)
+            s64 = sigma_of(x64)
+            gm["fp64_none"]["omega"] = [float(v) for v in zs[sel].real]
+            gm["sigma_rel_err_vs_fp64"] = float(np.linalg.norm(sig_none[sel] - s64) / np.linalg.norm(s64))
+            sys64.close()
+            del x64
         sys_g.close()
         del xg
 
@@ -371,6 +430,7 @@ def main():
             "e2e": {"value": e2e, "unit": "matvecs/s", "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 16,
                     "api": "bse_apply_h with pinned host psi/hpsi"},
             "gpu_launches": launches,
+            "spectrum": spec,
             "gmres": gm,
             "clocks": clocks,
             "cpu_baseline": cpu,

@@ -57,6 +57,7 @@ struct bse_handle {
   double* e_nk = nullptr;     // [Nk][Nb]
   double2* chi = nullptr;     // [Na][Na]
   double2* a_proj = nullptr;  // [Np][Nk*Nb]
+  float2* a_proj_f = nullptr; // FP32 copy for the reduced-precision forms
   double2* m_sr = nullptr;    // [Na*Np][Na*Np]
   double* jdiag = nullptr;    // [Na][Nk][Nb]
   double* twiddle = nullptr;  // [3][16][2] e^{+2 pi i j / nk_d}, j < nk_d
@@ -144,6 +145,10 @@ struct bse_dotfuse {
   int a_stride = 0, i = 0;
   const int* active = nullptr;
   int* status = nullptr;
+  // lazy Haydock normalisation: when scale_b is set, psi holds w_i unnormalised
+  // and the first kernel to read it rescales it in place, psi_v /= scale_b[v * scale_stride + scale_col]
+  const double* scale_b = nullptr;
+  int scale_col = 0, scale_stride = 0;
 };
 
 // H psi on device pointers (k_apply.cu); psi/hpsi [n_vec][N] double2, n_vec <= max_vec.
@@ -155,7 +160,9 @@ bool bse_apply_fuses_dot(const bse_handle* h);
 
 // tensor-core band<->grid path (k_tc.cu)
 bse_status bse_tc_prepare(bse_handle* h);
-bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec);
+// B operand of band->grid from psi (and, with fuse->scale_b set, the in-place rescaling of psi)
+bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_dotfuse* fuse);
+bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec);
 bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
                                const bse_dotfuse* fuse, bool wait_side);
 bse_status bse_kconv_bf16(bse_handle* h, int n_vec);

@@ -299,17 +299,26 @@ bse_status bse_sr_terms(bse_handle* h, const double2* psi, int n_vec) {
 bool bse_apply_fuses_dot(const bse_handle* h) { return h->prec == BSE_PREC_SPLIT_BF16; }
 
 bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, int n_vec, const bse_dotfuse* fuse) {
-  bse_status s = bse_sr_terms(h, psi, n_vec);
-  if (s != BSE_OK) return s;
+  bse_status s;
   switch (h->prec) {
     case BSE_PREC_FP64:
       if (fuse) return BSE_ERR_UNSUPPORTED;
+      s = bse_sr_terms(h, psi, n_vec);
+      if (s != BSE_OK) return s;
       return apply_simt<double>(h, psi, hpsi, n_vec);
     case BSE_PREC_FP32:
       if (fuse) return BSE_ERR_UNSUPPORTED;
+      s = bse_sr_terms(h, psi, n_vec);
+      if (s != BSE_OK) return s;
       return apply_simt<float>(h, psi, hpsi, n_vec);
     case BSE_PREC_SPLIT_BF16: {
-      s = bse_tc_band_to_grid(h, psi, n_vec);
+      // the operand pass runs first: it may rescale psi in place (lazy Haydock
+      // normalisation), and the short-range side stream forks after it
+      s = bse_tc_prep(h, psi, n_vec, fuse);
+      if (s != BSE_OK) return s;
+      s = bse_sr_terms(h, psi, n_vec);
+      if (s != BSE_OK) return s;
+      s = bse_tc_band_to_grid(h, n_vec);
       if (s != BSE_OK) return s;
       s = bse_kconv_bf16(h, n_vec);
       if (s != BSE_OK) return s;

@@ -683,6 +683,9 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   // a_i from the fused H psi epilogue when the form supports it and one pass covers all vectors
   const bool fuse_a = bse_apply_fuses_dot(h) && n_vec <= h->max_vec;
   const bool fuse_b = !reorth;
+  // v_{i+1} = w / b_{i+1} is applied by the next step's first kernel (in place)
+  // instead of a pass of its own
+  const bool lazy_scale = fuse_a && fuse_b;
   if (reorth) {
     // Gram-Schmidt partials need one row per basis vector
     TRY(dalloc(h, &partial, (size_t)n_vec * NBLK * (n_steps + 1) * sizeof(double2), "gs partials"));
@@ -735,6 +738,11 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
       f.i = i;
       f.active = active;
       f.status = status;
+      if (lazy_scale && i >= 1) {
+        f.scale_b = b_d;
+        f.scale_col = i;
+        f.scale_stride = n_steps + 1;
+      }
       loop_status = bse_apply_device(h, vc, w, n_vec, &f);     // w = H v_i, a_i = Re <v_i|w>
       if (loop_status != BSE_OK) break;
     } else {
@@ -755,7 +763,9 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
       BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, N, nullptr, 0, N, hpart));
       BSE_PROF(h, BSE_K_RECURSION, hay_b_finalize<<<n_vec, RB, 0, st>>>(hpart, NBLK, a_d, b_d, n_steps, i, active, steps_d, status));
     }
-    BSE_PROF(h, BSE_K_RECURSION, hay_scale<<<eg, 256, 0, st>>>(w, w, N, b_d, i + 1, n_steps + 1, active));   // v_{i+1}
+    if (!lazy_scale) {
+      BSE_PROF(h, BSE_K_RECURSION, hay_scale<<<eg, 256, 0, st>>>(w, w, N, b_d, i + 1, n_steps + 1, active));   // v_{i+1}
+    }
     if (reorth && i + 1 <= n_steps) {
       BSE_PROF(h, BSE_K_RECURSION, copy_vecs<<<eg, 256, 0, st>>>(w, basis + (size_t)(i + 1) * N, N, (long long)(n_steps + 1) * N));
     }

@@ -174,6 +174,10 @@ bse_status bse_setup_device(bse_handle* h, const bse_system_desc* d) {
     TRY(dev_alloc(h, &h->a_proj, (size_t)h->np * nkb * sizeof(double2), "a_proj"));
     TRY(dev_alloc(h, &h->m_sr, (size_t)h->na * h->np * h->na * h->np * sizeof(double2), "m_sr"));
     TRY(bse_cuda_check(h, cudaMemcpyAsync(h->a_proj, d->a_proj, (size_t)h->np * nkb * sizeof(double2), cudaMemcpyDefault, st), "copy a_proj"));
+    if (h->prec != BSE_PREC_FP64) {
+      TRY(dev_alloc(h, &h->a_proj_f, (size_t)h->np * nkb * sizeof(float2), "a_proj (fp32)"));
+      BSE_PROF(h, BSE_K_PREP, to_float2_kernel<<<1024, 256, 0, st>>>(h->a_proj, h->a_proj_f, (size_t)h->np * nkb));
+    }
     TRY(bse_cuda_check(h, cudaMemcpyAsync(h->m_sr, d->m_sr, (size_t)h->na * h->np * h->na * h->np * sizeof(double2), cudaMemcpyDefault, st), "copy m_sr"));
     TRY(dev_alloc(h, &h->sr_c, (size_t)h->max_vec * h->na * h->np * sizeof(double2), "sr_c"));
     TRY(dev_alloc(h, &h->sr_cp, (size_t)h->max_vec * h->na * h->np * sizeof(double2), "sr_cp"));

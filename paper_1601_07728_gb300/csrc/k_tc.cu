@@ -393,24 +393,40 @@ __device__ __forceinline__ void split2(float v, __nv_bfloat16& hi, __nv_bfloat16
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// Bpsi_k[j][q] (hi, lo): j = 2c + s, q = 2n + u; rows j >= 2Nc and q >= 2Nb are zero.
-__global__ void prep_bpsi(const double2* __restrict__ psi, __nv_bfloat16* __restrict__ hi,
-                          __nv_bfloat16* __restrict__ lo, int nk, int nb, int nc, int nn, int kp, int nnmax) {
-  const int k = blockIdx.x;
-  for (int e = threadIdx.x; e < nn * kp; e += blockDim.x) {
-    const int j = e / kp, q = e % kp;
-    const int c = j >> 1, s = j & 1, n = q >> 1, u = q & 1;
-    float val = 0.f;
-    if (c < nc && n < nb) {
-      const double2 ps = psi[((size_t)c * nk + k) * nb + n];
-      // s = 0: Re phi = Ur psi_r - Ui psi_i ; s = 1: Im phi = Ur psi_i + Ui psi_r
-      val = (float)(s == 0 ? (u == 0 ? ps.x : -ps.y) : (u == 0 ? ps.y : ps.x));
+// Bpsi_k[j][q] (hi, lo): j = 2c + s, q = 2n + u, one thread per psi element
+// (c, k, n).  Row j = 2c gives Re phi = Ur psi_r - Ui psi_i (q = 2n: psi_r,
+// q = 2n+1: -psi_i), row 2c+1 gives Im phi = Ur psi_i + Ui psi_r.  Entries with
+// q >= 2Nb stay zero (the buffer is zeroed once and never written there); rows
+// j >= 2Nc only feed output columns that are not stored.  With bco set, psi is
+// first divided in place by bco[v * stride + col] for active vectors v = c / na.
+__global__ void prep_bpsi(double2* __restrict__ psi, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                          int nk, int nb, int nc, int kp, int nnmax, int na, const double* __restrict__ bco, int col,
+                          int stride, const int* __restrict__ active) {
+  const size_t total = (size_t)nc * nk * nb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e % nb);
+    const size_t ck = e / nb;
+    const int k = (int)(ck % nk), c = (int)(ck / nk);
+    double2 ps = psi[e];
+    if (bco) {
+      const int v = c / na;
+      if (active[v]) {
+        const double inv = 1.0 / bco[(size_t)v * stride + col];
+        ps = make_double2(ps.x * inv, ps.y * inv);
+        psi[e] = ps;
+      }
     }
-    __nv_bfloat16 h, l;
-    split2(val, h, l);
-    const size_t o = ((size_t)k * nnmax + j) * kp + q;
-    hi[o] = h;
-    lo[o] = l;
+    const float re = (float)ps.x, im = (float)ps.y;
+    __nv_bfloat16 h0, l0, h1, l1, h2, l2;
+    split2(re, h0, l0);
+    split2(-im, h1, l1);
+    split2(im, h2, l2);
+    const size_t o0 = ((size_t)k * nnmax + 2 * c) * kp + 2 * n;
+    const size_t o1 = o0 + kp;
+    *reinterpret_cast<__nv_bfloat162*>(hi + o0) = __halves2bfloat162(h0, h1);
+    *reinterpret_cast<__nv_bfloat162*>(lo + o0) = __halves2bfloat162(l0, l1);
+    *reinterpret_cast<__nv_bfloat162*>(hi + o1) = __halves2bfloat162(h2, h0);
+    *reinterpret_cast<__nv_bfloat162*>(lo + o1) = __halves2bfloat162(l2, l0);
   }
 }
 
@@ -465,13 +481,18 @@ __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
 // Epilogue with NA core states per thread: one thread per (k, n) of vector
 // v = blockIdx.y computes all NA outputs, so A[:, kn] and psi[v][:][kn] are
 // read once; c' and chi are staged in shared memory as FP32.
-template <int NA>
+// out[c][k][n] = sum_split part + E psi - chi psi + short-range out for NA
+// core states, G of them per thread (NA / G threads per (k, n): more loads in
+// flight for this latency-bound pass); the projectors are read in FP32.
+template <int NA, int G>
 __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ part, int nsplit,
                                                     const double2* __restrict__ psi, double2* __restrict__ out,
                                                     const double* __restrict__ e_nk, const double2* __restrict__ chi,
-                                                    const double2* __restrict__ a_proj,
+                                                    const float2* __restrict__ a_proj,
                                                     const double2* __restrict__ srcp, int nk, int nb, int np, int nc,
                                                     bse_dotfuse f) {
+  constexpr int NG = NA / G;
+  constexpr int PU = 12;   // projector loads in flight per thread
   __shared__ float2 cps[NA * BSE_MAX_PROJ];
   __shared__ float2 chs[NA * NA];
   const size_t nkb = (size_t)nk * nb;
@@ -483,46 +504,42 @@ __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ p
   for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) chs[i] = make_float2((float)chi[i].x, (float)chi[i].y);
   __syncthreads();
   double dre = 0.0, dim = 0.0;
-  for (size_t kn = blockIdx.x * (size_t)blockDim.x + threadIdx.x; kn < nkb; kn += (size_t)gridDim.x * blockDim.x) {
+  const size_t total = nkb * NG;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t kn = e / NG;
+    const int a0 = (int)(e % NG) * G;
     const int k = (int)(kn / nb), n = (int)(kn % nb);
-    double2 ps[NA];
-    float2 pf[NA], acc[NA];
+    float2 pf[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      ps[a] = psi[(size_t)(v * NA + a) * nkb + kn];
-      pf[a] = make_float2((float)ps[a].x, (float)ps[a].y);
-      acc[a] = make_float2(0.f, 0.f);
+    for (int b = 0; b < NA; ++b) {
+      const double2 d = psi[(size_t)(v * NA + b) * nkb + kn];
+      pf[b] = make_float2((float)d.x, (float)d.y);
     }
-    int p = 0;
-    for (; p + 4 <= np; p += 4) {
-      double2 apd[4];
+    float2 acc[G];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) apd[u] = a_proj[(size_t)(p + u) * nkb + kn];   // 4 loads in flight
+    for (int g = 0; g < G; ++g) acc[g] = make_float2(0.f, 0.f);
+    for (int p0 = 0; p0 < np; p0 += PU) {
+      float2 ap[PU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float2 ap = make_float2((float)apd[u].x, (float)apd[u].y);
+      for (int u = 0; u < PU; ++u)
+        ap[u] = p0 + u < np ? a_proj[(size_t)(p0 + u) * nkb + kn] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-          const float2 q = cps[a * np + p + u];
-          acc[a].x += ap.x * q.x + ap.y * q.y;   // conj(A) c'
-          acc[a].y += ap.x * q.y - ap.y * q.x;
+      for (int u = 0; u < PU; ++u) {
+        if (p0 + u < np) {
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const float2 q = cps[(a0 + g) * np + p0 + u];
+            acc[g].x += ap[u].x * q.x + ap[u].y * q.y;   // conj(A) c'
+            acc[g].y += ap[u].x * q.y - ap[u].y * q.x;
+          }
         }
       }
     }
-    for (; p < np; ++p) {
-      const double2 apd = a_proj[(size_t)p * nkb + kn];
-      const float2 ap = make_float2((float)apd.x, (float)apd.y);
+    const double e_kn = e_nk[kn];
 #pragma unroll
-      for (int a = 0; a < NA; ++a) {
-        const float2 q = cps[a * np + p];
-        acc[a].x += ap.x * q.x + ap.y * q.y;
-        acc[a].y += ap.x * q.y - ap.y * q.x;
-      }
-    }
-    const double e = e_nk[kn];
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      float rx = acc[a].x, ry = acc[a].y;
+    for (int g = 0; g < G; ++g) {
+      const int a = a0 + g;
+      float rx = acc[g].x, ry = acc[g].y;
 #pragma unroll
       for (int b = 0; b < NA; ++b) {
         const float2 ch = chs[a * NA + b];
@@ -536,10 +553,11 @@ __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ p
         lx += t.x;
         ly += t.y;
       }
-      const double2 val = make_double2(lx + (double)rx + e * ps[a].x, ly + (double)ry + e * ps[a].y);
+      const double2 ps = psi[(size_t)c * nkb + kn];
+      const double2 val = make_double2(lx + (double)rx + e_kn * ps.x, ly + (double)ry + e_kn * ps.y);
       out[(size_t)c * nkb + kn] = val;
-      dre += ps[a].x * val.x + ps[a].y * val.y;
-      dim += ps[a].x * val.y - ps[a].y * val.x;
+      dre += ps.x * val.x + ps.y * val.y;
+      dim += ps.x * val.y - ps.y * val.x;
     }
   }
   if (f.partial) fused_dot_tail(f, dre, dim);
@@ -712,6 +730,7 @@ bse_status bse_tc_prepare(bse_handle* h) {
   ts->err = (int*)h->tmap;
   cudaMemsetAsync(ts->err, 0, 256, h->stream);
   cudaMemsetAsync(h->bphi, 0, 2 * nbf * sizeof(__nv_bfloat16), h->stream);
+  cudaMemsetAsync(h->bpsi, 0, 2 * nbp * sizeof(__nv_bfloat16), h->stream);
   const int kp = ts->kp;
   bool ok = make_map(&ts->a2_hi, h->u_hi, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
             make_map(&ts->a2_lo, h->u_lo, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
@@ -728,14 +747,28 @@ void bse_tc_free(bse_handle* h) {
   h->tmap_host = nullptr;
 }
 
-bse_status bse_tc_band_to_grid(bse_handle* h, const double2* psi, int n_vec) {
+bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_dotfuse* fuse) {
+  TcState* ts = (TcState*)h->tmap_host;
+  const int nc = n_vec * h->na;
+  const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
+  const size_t total = (size_t)nc * h->nk * h->nb;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)8 * ts->sms);
+  const bool scale = fuse && fuse->scale_b;
+  BSE_PROF(h, BSE_K_PREP,
+           prep_bpsi<<<blocks, 256, 0, h->stream>>>(const_cast<double2*>(psi), h->bpsi, h->bpsi + nbp, h->nk, h->nb,
+                                                    nc, ts->kp, ts->nnmax, h->na, scale ? fuse->scale_b : nullptr,
+                                                    scale ? fuse->scale_col : 0, scale ? fuse->scale_stride : 0,
+                                                    scale ? fuse->active : nullptr));
+  return bse_cuda_check(h, cudaGetLastError(), "prep_bpsi launch");
+}
+
+bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec) {
   TcState* ts = (TcState*)h->tmap_host;
   const int nc = n_vec * h->na;
   const int nn = round_up(2 * nc, 16);
   const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
   __nv_bfloat16* bh = h->bpsi;
   __nv_bfloat16* bl = h->bpsi + nbp;
-  BSE_PROF(h, BSE_K_PREP, prep_bpsi<<<h->nk, 256, 0, h->stream>>>(psi, bh, bl, h->nk, h->nb, nc, nn, ts->kp, ts->nnmax));
   CUtensorMap b_hi, b_lo;
   if (!make_map(&b_hi, bh, ts->kp, nn, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn) ||
       !make_map(&b_lo, bl, ts->kp, nn, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn))
@@ -795,17 +828,23 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   if (blocks > BSE_FINAL_BLOCKS) blocks = BSE_FINAL_BLOCKS;
   bse_dotfuse f = fuse ? *fuse : bse_dotfuse();
   const size_t nkb = (size_t)h->nk * h->nb;
-  int bk = (int)((nkb + 63) / 64);   // 64-thread blocks: more blocks in flight for this latency-bound pass
-  if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
-  const dim3 gk((unsigned)bk, (unsigned)n_vec);
+  auto final_grid = [&](int ng) {
+    int bk = (int)((nkb * ng + 255) / 256);
+    if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
+    return dim3((unsigned)bk, (unsigned)n_vec);
+  };
+  const double2* srp = h->sr_cp;
+  const float2* apf = h->a_proj_f;
   if (h->na == 6) {
     BSE_PROF(h, BSE_K_PREP,
-             g2b_final_na<6><<<gk, 64, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
-                                                       h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
+             (g2b_final_na<6, 2><<<final_grid(3), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi,
+                                                                       h->e_nk, h->chi, apf, srp, h->nk, h->nb,
+                                                                       h->np, nc, f)));
   } else if (h->na == 1) {
     BSE_PROF(h, BSE_K_PREP,
-             g2b_final_na<1><<<gk, 64, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi,
-                                                       h->a_proj, h->sr_cp, h->nk, h->nb, h->np, nc, f));
+             (g2b_final_na<1, 1><<<final_grid(1), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi,
+                                                                       h->e_nk, h->chi, apf, srp, h->nk, h->nb,
+                                                                       h->np, nc, f)));
   } else {
     BSE_PROF(h, BSE_K_PREP,
              g2b_final<<<dim3((unsigned)blocks, (unsigned)n_vec), 256, 0, h->stream>>>(
