@@ -13,7 +13,7 @@
 #define BSE_MAX_ALPHA 16
 #define BSE_MAX_NK_AXIS 16
 #define BSE_MAX_PROJ 64
-#define BSE_FINAL_BLOCKS 512   // blocks per vector of the fused grid->band epilogue
+#define BSE_FINAL_BLOCKS 1024  // blocks per vector of the fused grid->band epilogue
 
 // ---------------------------------------------------------------------------
 // complex helpers (interleaved re, im)

@@ -29,6 +29,12 @@ template <typename C> __device__ __forceinline__ C from_d2(double2 v) {
   r.y = v.y;
   return r;
 }
+template <typename C> __device__ __forceinline__ C from_d2(float2 v) {
+  C r;
+  r.x = v.x;
+  r.y = v.y;
+  return r;
+}
 
 // ---------------------------------------------------------------------------
 // band -> grid:  phi[k][c0+cc][x] = sum_n U[k][x][n] psi[c0+cc][k][n]
@@ -158,8 +164,8 @@ __global__ void __launch_bounds__(256) g2b_simt(
 // columns and all Np functions; part[b][c][p] (accumulated in T).
 // ---------------------------------------------------------------------------
 constexpr int SRK = 64, SRC = 16;
-template <typename T>
-__global__ void __launch_bounds__(256) sr_in_partial(const double2* __restrict__ a_proj,
+template <typename T, typename AT>
+__global__ void __launch_bounds__(256) sr_in_partial(const AT* __restrict__ a_proj,
                                                      const double2* __restrict__ psi,
                                                      double2* __restrict__ part, int nkb, int np, int nc) {
   typedef typename Cx<T>::type C;
@@ -264,8 +270,15 @@ void launch_sr_in(bse_handle* h, const double2* psi, int nc, int nkb, int nblk) 
   typedef typename Cx<T>::type C;
   dim3 g((unsigned)nblk, (unsigned)((nc + SRC - 1) / SRC));
   const size_t smem = (size_t)(h->np + SRC) * (SRK + 1) * sizeof(C);
-  cudaFuncSetAttribute(sr_in_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  BSE_PROF(h, BSE_K_SR_IN, sr_in_partial<T><<<g, 256, smem, h->side>>>(h->a_proj, psi, h->sr_part, nkb, h->np, nc));
+  if (h->a_proj_f) {   // reduced-precision forms: FP32 copy of the projectors (half the bytes)
+    cudaFuncSetAttribute(sr_in_partial<T, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    BSE_PROF(h, BSE_K_SR_IN,
+             (sr_in_partial<T, float2><<<g, 256, smem, h->side>>>(h->a_proj_f, psi, h->sr_part, nkb, h->np, nc)));
+  } else {
+    cudaFuncSetAttribute(sr_in_partial<T, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    BSE_PROF(h, BSE_K_SR_IN,
+             (sr_in_partial<T, double2><<<g, 256, smem, h->side>>>(h->a_proj, psi, h->sr_part, nkb, h->np, nc)));
+  }
 }
 
 }  // namespace

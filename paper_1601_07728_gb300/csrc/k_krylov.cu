@@ -15,6 +15,7 @@ namespace {
 
 constexpr int RB = 256;      // threads per reduction block
 constexpr int NBLK = 296;    // partial-sum blocks per vector (2 x 148)
+constexpr int UBLK = 768;    // blocks per vector of the Haydock update (about one element per thread)
 
 enum { ST_BREAKDOWN = 1, ST_NAN = 2 };
 
@@ -640,7 +641,7 @@ __global__ void __launch_bounds__(RB) hay_update_fin(double2* __restrict__ w, co
 namespace {
 // Grow-only Haydock workspace of a handle: three vectors, partial sums, flags.
 size_t hay_ws_bytes(long long N, int n_vec) {
-  return 3 * (size_t)n_vec * N * sizeof(double2) + (size_t)n_vec * NBLK * sizeof(double2) +
+  return 3 * (size_t)n_vec * N * sizeof(double2) + (size_t)n_vec * UBLK * sizeof(double2) +
          (size_t)n_vec * BSE_FINAL_BLOCKS * sizeof(double2) + 256 + (size_t)n_vec * sizeof(int) + 256;
 }
 
@@ -669,7 +670,7 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   {
     TRY(hay_reserve(h, n_vec));
     const size_t bv = 3 * (size_t)n_vec * N * sizeof(double2);
-    const size_t bp = (size_t)n_vec * NBLK * sizeof(double2);
+    const size_t bp = (size_t)n_vec * UBLK * sizeof(double2);
     const size_t bf = (size_t)n_vec * BSE_FINAL_BLOCKS * sizeof(double2);
     char* p = (char*)h->ws;
     v3 = (double2*)p;
@@ -753,7 +754,8 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
     }
     if (fuse_b) {
       BSE_PROF(h, BSE_K_RECURSION,
-               hay_update_fin<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, vc, vp, N, a_d, b_d, n_steps, i, active, hpart,
+               hay_update_fin<<<dim3(std::min<long long>(UBLK, (N + RB - 1) / RB), n_vec), RB, 0, st>>>(
+                   w, vc, vp, N, a_d, b_d, n_steps, i, active, hpart,
                                                                  counters + 1, steps_d, status));
     } else {
       BSE_PROF(h, BSE_K_RECURSION, hay_update<<<dim3(NBLK, n_vec), RB, 0, st>>>(w, vc, vp, N, a_d, b_d, n_steps, i, active, hpart));

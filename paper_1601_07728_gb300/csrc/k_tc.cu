@@ -402,6 +402,14 @@ __device__ __forceinline__ void split2(float v, __nv_bfloat16& hi, __nv_bfloat16
 __global__ void prep_bpsi(double2* __restrict__ psi, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                           int nk, int nb, int nc, int kp, int nnmax, int na, const double* __restrict__ bco, int col,
                           int stride, const int* __restrict__ active) {
+  constexpr int MAXV = 64;
+  __shared__ double sinv[MAXV];   // 1 / b per vector (0 = leave unscaled), one FP64 division per block
+  const int nvec = nc / na;
+  if (bco) {
+    for (int v = threadIdx.x; v < nvec && v < MAXV; v += blockDim.x)
+      sinv[v] = active[v] ? 1.0 / bco[(size_t)v * stride + col] : 0.0;
+    __syncthreads();
+  }
   const size_t total = (size_t)nc * nk * nb;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int n = (int)(e % nb);
@@ -410,8 +418,8 @@ __global__ void prep_bpsi(double2* __restrict__ psi, __nv_bfloat16* __restrict__
     double2 ps = psi[e];
     if (bco) {
       const int v = c / na;
-      if (active[v]) {
-        const double inv = 1.0 / bco[(size_t)v * stride + col];
+      const double inv = v < MAXV ? sinv[v] : (active[v] ? 1.0 / bco[(size_t)v * stride + col] : 0.0);
+      if (inv != 0.0) {
         ps = make_double2(ps.x * inv, ps.y * inv);
         psi[e] = ps;
       }
@@ -547,14 +555,15 @@ __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ p
         ry -= ch.x * pf[b].y + ch.y * pf[b].x;
       }
       const int c = v * NA + a;
-      double lx = 0.0, ly = 0.0;
+      // split-K partials (FP32 tensor-core accumulators) summed in FP32 with
+      // the FP32 short-range and spin-orbit terms; E psi and the sum in FP64
       for (int sp = 0; sp < nsplit; ++sp) {
         const float2 t = part[(((size_t)sp * nk + k) * nc + c) * nb + n];
-        lx += t.x;
-        ly += t.y;
+        rx += t.x;
+        ry += t.y;
       }
       const double2 ps = psi[(size_t)c * nkb + kn];
-      const double2 val = make_double2(lx + (double)rx + e_kn * ps.x, ly + (double)ry + e_kn * ps.y);
+      const double2 val = make_double2((double)rx + e_kn * ps.x, (double)ry + e_kn * ps.y);
       out[(size_t)c * nkb + kn] = val;
       dre += ps.x * val.x + ps.y * val.y;
       dim += ps.x * val.y - ps.y * val.x;
@@ -680,6 +689,10 @@ int pick_stages(int nn) {
   const int stage = 2 * TC_M * 128 + 2 * nn * 128;
   int s = (SMEM_BUDGET - 1024 - 256) / stage;
   if (s > 8) s = 8;
+  // narrow (HBM-bound) tiles: four stages (~150 KB) keep ~25 MB in flight over
+  // the GPU, and leave shared memory for the short-range kernels of the side
+  // stream to run on the same SMs during the GEMM
+  if (nn <= 32 && s > 4) s = 4;
   return s;
 }
 
@@ -837,7 +850,7 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   const float2* apf = h->a_proj_f;
   if (h->na == 6) {
     BSE_PROF(h, BSE_K_PREP,
-             (g2b_final_na<6, 2><<<final_grid(3), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi,
+             (g2b_final_na<6, 1><<<final_grid(6), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi,
                                                                        h->e_nk, h->chi, apf, srp, h->nk, h->nb,
                                                                        h->np, nc, f)));
   } else if (h->na == 1) {
