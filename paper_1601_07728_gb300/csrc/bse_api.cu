@@ -78,7 +78,7 @@ bse_status stage_out(bse_handle* h, Staged& s, void* p, size_t bytes, const char
 void free_handle(bse_handle* h) {
   if (!h) return;
   void* ptrs[] = {h->e_nk, h->chi, h->a_proj, h->a_proj_f, h->m_sr, h->jdiag, h->twiddle, h->u, h->w, h->u_hi,
-                  h->u_lo, h->ut_hi, h->ut_lo, h->phi, h->sr_c, h->sr_cp, h->sr_part, h->bpsi, h->bphi,
+                  h->u_lo, h->ut_hi, h->ut_lo, h->phi, h->sr_c, h->sr_cp, h->sr_part, h->bpsi, h->psi_f, h->bphi,
                   h->part, h->tmap};
   for (void* p : ptrs)
     if (p) cudaFree(p);

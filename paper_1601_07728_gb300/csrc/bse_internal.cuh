@@ -76,6 +76,7 @@ struct bse_handle {
   double2* sr_cp = nullptr;   // [max_vec][Na*Np]
   double2* sr_part = nullptr; // [ceil(Nk*Nb/64)][max_vec*Na][Np] split-K partial projections
   __nv_bfloat16* bpsi = nullptr;    // SPLIT_BF16: [Nk][2][Nrow][2Nb] B operand of band->grid
+  float2* psi_f = nullptr;          // SPLIT_BF16: FP32 copy of the operand psi [max_vec][N] (operand pass)
   __nv_bfloat16* bphi = nullptr;    // SPLIT_BF16: hi/lo K-tiled [Nk][ceil(Nx/64)][Nrow][64] B operand of grid->band
   float* part = nullptr;            // SPLIT_BF16: split-K partial tiles
   void* tmap = nullptr;             // SPLIT_BF16: tensor maps (device copy)
@@ -144,11 +145,20 @@ struct bse_dotfuse {
   double* a = nullptr;          // a[v * a_stride + i]
   int a_stride = 0, i = 0;
   const int* active = nullptr;
-  int* status = nullptr;
-  // lazy Haydock normalisation: when scale_b is set, psi holds w_i unnormalised
-  // and the first kernel to read it rescales it in place, psi_v /= scale_b[v * scale_stride + scale_col]
-  const double* scale_b = nullptr;
-  int scale_col = 0, scale_stride = 0;
+  int* status = nullptr;        // bit 0: breakdown, bit 1: non-finite value
+  // deferred mode: the epilogue only writes its per-block partials of
+  // <psi|H psi>; the Haydock update kernel reduces them (in every block, in a
+  // fixed order) instead of a last-block reduction here
+  bool deferred = false;
+  // lazy normalisation (deferred mode, step i >= 1): psi holds w_i
+  // unnormalised; the operand pass reduces norm_part [n_vec][norm_n] to
+  // b_i = |w_i|, records b_i (bco[v * (a_stride + 1) + i]), the step count and
+  // the breakdown test, and divides psi by b_i in place
+  const double2* norm_part = nullptr;
+  int norm_n = 0;
+  double* bco = nullptr;
+  int* active_rw = nullptr;
+  int* steps = nullptr;
 };
 
 // H psi on device pointers (k_apply.cu); psi/hpsi [n_vec][N] double2, n_vec <= max_vec.
@@ -160,8 +170,10 @@ bool bse_apply_fuses_dot(const bse_handle* h);
 
 // tensor-core band<->grid path (k_tc.cu)
 bse_status bse_tc_prepare(bse_handle* h);
-// B operand of band->grid from psi (and, with fuse->scale_b set, the in-place rescaling of psi)
+// B operand of band->grid from psi (and, with fuse->norm_part set, the lazy normalisation of psi)
 bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_dotfuse* fuse);
+// blocks per vector of the grid->band epilogue (the number of <psi|H psi> partials it writes)
+int bse_tc_final_blocks(const bse_handle* h);
 bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec);
 bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
                                const bse_dotfuse* fuse, bool wait_side);

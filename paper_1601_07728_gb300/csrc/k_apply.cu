@@ -164,9 +164,9 @@ __global__ void __launch_bounds__(256) g2b_simt(
 // columns and all Np functions; part[b][c][p] (accumulated in T).
 // ---------------------------------------------------------------------------
 constexpr int SRK = 64, SRC = 16;
-template <typename T, typename AT>
+template <typename T, typename AT, typename PT>
 __global__ void __launch_bounds__(256) sr_in_partial(const AT* __restrict__ a_proj,
-                                                     const double2* __restrict__ psi,
+                                                     const PT* __restrict__ psi,
                                                      double2* __restrict__ part, int nkb, int np, int nc) {
   typedef typename Cx<T>::type C;
   extern __shared__ __align__(16) unsigned char sr_smem[];
@@ -270,14 +270,22 @@ void launch_sr_in(bse_handle* h, const double2* psi, int nc, int nkb, int nblk) 
   typedef typename Cx<T>::type C;
   dim3 g((unsigned)nblk, (unsigned)((nc + SRC - 1) / SRC));
   const size_t smem = (size_t)(h->np + SRC) * (SRK + 1) * sizeof(C);
-  if (h->a_proj_f) {   // reduced-precision forms: FP32 copy of the projectors (half the bytes)
-    cudaFuncSetAttribute(sr_in_partial<T, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (h->a_proj_f && h->psi_f && h->prec == BSE_PREC_SPLIT_BF16) {
+    // tensor-core form: FP32 projectors and the FP32 psi of the operand pass
+    cudaFuncSetAttribute(sr_in_partial<T, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     BSE_PROF(h, BSE_K_SR_IN,
-             (sr_in_partial<T, float2><<<g, 256, smem, h->side>>>(h->a_proj_f, psi, h->sr_part, nkb, h->np, nc)));
+             (sr_in_partial<T, float2, float2><<<g, 256, smem, h->side>>>(h->a_proj_f, h->psi_f, h->sr_part, nkb,
+                                                                           h->np, nc)));
+  } else if (h->a_proj_f) {   // FP32 form: FP32 copy of the projectors (half the bytes)
+    cudaFuncSetAttribute(sr_in_partial<T, float2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    BSE_PROF(h, BSE_K_SR_IN,
+             (sr_in_partial<T, float2, double2><<<g, 256, smem, h->side>>>(h->a_proj_f, psi, h->sr_part, nkb, h->np,
+                                                                            nc)));
   } else {
-    cudaFuncSetAttribute(sr_in_partial<T, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(sr_in_partial<T, double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     BSE_PROF(h, BSE_K_SR_IN,
-             (sr_in_partial<T, double2><<<g, 256, smem, h->side>>>(h->a_proj, psi, h->sr_part, nkb, h->np, nc)));
+             (sr_in_partial<T, double2, double2><<<g, 256, smem, h->side>>>(h->a_proj, psi, h->sr_part, nkb, h->np,
+                                                                             nc)));
   }
 }
 

@@ -15,7 +15,7 @@ namespace {
 
 constexpr int RB = 256;      // threads per reduction block
 constexpr int NBLK = 296;    // partial-sum blocks per vector (2 x 148)
-constexpr int UBLK = 768;    // blocks per vector of the Haydock update (about one element per thread)
+constexpr int UBLK = 296;    // blocks per vector of the Haydock update (its |w|^2 partials are reduced again by every block of the next operand pass)
 
 enum { ST_BREAKDOWN = 1, ST_NAN = 2 };
 
@@ -639,6 +639,97 @@ __global__ void __launch_bounds__(RB) hay_update_fin(double2* __restrict__ w, co
 }  // namespace
 
 namespace {
+// Deterministic block-wide sum of part[0..n).x; every block of a grid gets the
+// same value (fixed element-to-thread map and order).  All threads return it.
+__device__ double block_sum_x_k(const double2* __restrict__ part, int n) {
+  __shared__ double ws[RB / 32];
+  __shared__ double tot;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += RB) acc += part[i].x;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < RB / 32; ++w) s += ws[w];
+    tot = s;
+  }
+  __syncthreads();
+  const double r = tot;
+  __syncthreads();
+  return r;
+}
+
+// Haydock update with deferred reductions (no atomics, no last block): every
+// block reduces the epilogue's partials of <v_i|H v_i> to a_i itself (block 0
+// records it), applies w -= a_i v_i + b_i v_{i-1}, and writes its partial of
+// |w|^2, which the next step's operand pass (or hay_norm_final) reduces.
+__global__ void __launch_bounds__(RB) hay_update_deferred(double2* __restrict__ w, const double2* __restrict__ vc,
+                                                          const double2* __restrict__ vp, long long N,
+                                                          const double2* __restrict__ fpart, int nfb,
+                                                          double* __restrict__ a, const double* __restrict__ bco,
+                                                          int n_steps, int i, const int* __restrict__ active,
+                                                          double2* __restrict__ partial, int* status) {
+  const int v = blockIdx.y;
+  if (!active[v]) {
+    if (threadIdx.x == 0) partial[(size_t)v * gridDim.x + blockIdx.x] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double ai = block_sum_x_k(fpart + (size_t)v * nfb, nfb);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a[(size_t)v * n_steps + i] = ai;
+    if (!isfinite(ai)) atomicOr(status, ST_NAN);
+  }
+  const double bi = i >= 1 ? bco[(size_t)v * (n_steps + 1) + i] : 0.0;
+  double acc = 0.0;
+  for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < N; e += (long long)gridDim.x * RB) {
+    const size_t o = (size_t)v * N + e;
+    double2 ww = w[o];
+    const double2 c = vc[o];
+    ww.x -= ai * c.x;
+    ww.y -= ai * c.y;
+    if (i >= 1) {
+      const double2 p = vp[o];
+      ww.x -= bi * p.x;
+      ww.y -= bi * p.y;
+    }
+    w[o] = ww;
+    acc += ww.x * ww.x + ww.y * ww.y;
+  }
+  __shared__ double ws[RB / 32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < RB / 32; ++k) s += ws[k];
+    partial[(size_t)v * gridDim.x + blockIdx.x] = make_double2(s, 0.0);
+  }
+}
+
+// b_col = |w| from the update's partials after the last step (one block per
+// vector): records b, the step count and the breakdown test.
+__global__ void __launch_bounds__(RB) hay_norm_final(const double2* __restrict__ partial, int nhp,
+                                                     const double* __restrict__ a, double* __restrict__ bco,
+                                                     int n_steps, int col, int* active, int* steps, int* status) {
+  const int v = blockIdx.x;
+  const double s = block_sum_x_k(partial + (size_t)v * nhp, nhp);
+  if (threadIdx.x != 0 || !active[v]) return;
+  const double bn = sqrt(s);
+  const double ai = a[(size_t)v * n_steps + col - 1];
+  bco[(size_t)v * (n_steps + 1) + col] = bn;
+  steps[v] = col;
+  if (!isfinite(bn) || !isfinite(ai)) {
+    active[v] = 0;
+    atomicOr(status, ST_NAN);
+  } else if (bn <= 1e-12 * fmax(1.0, fabs(ai))) {
+    active[v] = 0;
+    atomicOr(status, ST_BREAKDOWN);
+  }
+}
+}  // namespace
+
+namespace {
 // Grow-only Haydock workspace of a handle: three vectors, partial sums, flags.
 size_t hay_ws_bytes(long long N, int n_vec) {
   return 3 * (size_t)n_vec * N * sizeof(double2) + (size_t)n_vec * UBLK * sizeof(double2) +
@@ -684,9 +775,12 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   // a_i from the fused H psi epilogue when the form supports it and one pass covers all vectors
   const bool fuse_a = bse_apply_fuses_dot(h) && n_vec <= h->max_vec;
   const bool fuse_b = !reorth;
-  // v_{i+1} = w / b_{i+1} is applied by the next step's first kernel (in place)
-  // instead of a pass of its own
-  const bool lazy_scale = fuse_a && fuse_b;
+  // deferred form (tensor-core path, no re-orthogonalisation): a_i and b_{i+1}
+  // are reduced by their consumers (the update kernel, the next operand pass),
+  // and v_{i+1} = w / b_{i+1} is applied in place by the next operand pass
+  const bool lazy_scale = fuse_a && fuse_b && n_vec <= 64;
+  const int ublk = (int)std::min<long long>(UBLK, (N + RB - 1) / RB);
+  const int nfb = fuse_a ? bse_tc_final_blocks(h) : 0;
   if (reorth) {
     // Gram-Schmidt partials need one row per basis vector
     TRY(dalloc(h, &partial, (size_t)n_vec * NBLK * (n_steps + 1) * sizeof(double2), "gs partials"));
@@ -739,10 +833,15 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
       f.i = i;
       f.active = active;
       f.status = status;
-      if (lazy_scale && i >= 1) {
-        f.scale_b = b_d;
-        f.scale_col = i;
-        f.scale_stride = n_steps + 1;
+      if (lazy_scale) {
+        f.deferred = true;
+        if (i >= 1) {
+          f.norm_part = hpart;
+          f.norm_n = ublk;
+          f.bco = b_d;
+          f.active_rw = active;
+          f.steps = steps_d;
+        }
       }
       loop_status = bse_apply_device(h, vc, w, n_vec, &f);     // w = H v_i, a_i = Re <v_i|w>
       if (loop_status != BSE_OK) break;
@@ -752,9 +851,13 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
       BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(vc, N, w, N, N, hpart));
       BSE_PROF(h, BSE_K_RECURSION, hay_a_finalize<<<n_vec, RB, 0, st>>>(hpart, NBLK, a_d, n_steps, i, active, status));
     }
-    if (fuse_b) {
+    if (lazy_scale) {
       BSE_PROF(h, BSE_K_RECURSION,
-               hay_update_fin<<<dim3(std::min<long long>(UBLK, (N + RB - 1) / RB), n_vec), RB, 0, st>>>(
+               hay_update_deferred<<<dim3(ublk, n_vec), RB, 0, st>>>(w, vc, vp, N, fpart, nfb, a_d, b_d, n_steps, i,
+                                                                     active, hpart, status));
+    } else if (fuse_b) {
+      BSE_PROF(h, BSE_K_RECURSION,
+               hay_update_fin<<<dim3(ublk, n_vec), RB, 0, st>>>(
                    w, vc, vp, N, a_d, b_d, n_steps, i, active, hpart,
                                                                  counters + 1, steps_d, status));
     } else {
@@ -775,6 +878,10 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
     vp = vc;
     vc = w;
     w = t;
+  }
+  if (lazy_scale && loop_status == BSE_OK && n_steps >= 1) {
+    BSE_PROF(h, BSE_K_RECURSION,
+             hay_norm_final<<<n_vec, RB, 0, st>>>(hpart, ublk, a_d, b_d, n_steps, n_steps, active, steps_d, status));
   }
   if (!capturing) break;
   // end the capture on every path; launch the graph, or re-run eagerly

@@ -393,21 +393,67 @@ __device__ __forceinline__ void split2(float v, __nv_bfloat16& hi, __nv_bfloat16
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// Deterministic block-wide sum of part[0..n).x (fixed element-to-thread map and
+// order, so every block of a grid obtains the same value); all threads return it.
+__device__ double block_sum_x(const double2* __restrict__ part, int n) {
+  __shared__ double ws[32];
+  __shared__ double tot;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i].x;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    tot = s;
+  }
+  __syncthreads();
+  const double r = tot;
+  __syncthreads();
+  return r;
+}
+
 // Bpsi_k[j][q] (hi, lo): j = 2c + s, q = 2n + u, one thread per psi element
 // (c, k, n).  Row j = 2c gives Re phi = Ur psi_r - Ui psi_i (q = 2n: psi_r,
 // q = 2n+1: -psi_i), row 2c+1 gives Im phi = Ur psi_i + Ui psi_r.  Entries with
 // q >= 2Nb stay zero (the buffer is zeroed once and never written there); rows
-// j >= 2Nc only feed output columns that are not stored.  With bco set, psi is
-// first divided in place by bco[v * stride + col] for active vectors v = c / na.
-__global__ void prep_bpsi(double2* __restrict__ psi, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                          int nk, int nb, int nc, int kp, int nnmax, int na, const double* __restrict__ bco, int col,
-                          int stride, const int* __restrict__ active) {
-  constexpr int MAXV = 64;
-  __shared__ double sinv[MAXV];   // 1 / b per vector (0 = leave unscaled), one FP64 division per block
+// j >= 2Nc only feed output columns that are not stored.  psi_f receives psi
+// rounded to FP32 for the FP32 terms of the epilogue and the short range.
+// With f.norm_part set (lazy Haydock normalisation, step i = f.i): every block
+// reduces |w_i|^2 of each vector from the update's partials (same order in
+// every block), block 0 records b_i = |w_i|, the step count and the breakdown
+// test, and psi is divided by b_i in place for vectors that stay active.
+constexpr int PREP_MAXV = 64;
+__global__ void __launch_bounds__(256) prep_bpsi(double2* __restrict__ psi, __nv_bfloat16* __restrict__ hi,
+                                                 __nv_bfloat16* __restrict__ lo, float2* __restrict__ psi_f, int nk,
+                                                 int nb, int nc, int kp, int nnmax, int na, bse_dotfuse f) {
+  __shared__ double sinv[PREP_MAXV];   // 1/b_i per vector, 0 = leave unscaled
   const int nvec = nc / na;
-  if (bco) {
-    for (int v = threadIdx.x; v < nvec && v < MAXV; v += blockDim.x)
-      sinv[v] = active[v] ? 1.0 / bco[(size_t)v * stride + col] : 0.0;
+  if (f.norm_part) {
+    for (int v = 0; v < nvec; ++v) {
+      const double s = block_sum_x(f.norm_part + (size_t)v * f.norm_n, f.norm_n);
+      if (threadIdx.x == 0) {
+        double inv = 0.0;
+        if (f.active_rw[v]) {
+          const double bn = sqrt(s);
+          const double ai = f.a[(size_t)v * f.a_stride + f.i - 1];
+          int st = 0;
+          if (!isfinite(bn) || !isfinite(ai)) st = 2;
+          else if (bn <= 1e-12 * fmax(1.0, fabs(ai))) st = 1;
+          if (blockIdx.x == 0) {
+            f.bco[(size_t)v * (f.a_stride + 1) + f.i] = bn;
+            f.steps[v] = f.i;
+            if (st) {
+              f.active_rw[v] = 0;
+              atomicOr(f.status, st);
+            }
+          }
+          if (!st) inv = 1.0 / bn;
+        }
+        sinv[v] = inv;
+      }
+    }
     __syncthreads();
   }
   const size_t total = (size_t)nc * nk * nb;
@@ -416,15 +462,15 @@ __global__ void prep_bpsi(double2* __restrict__ psi, __nv_bfloat16* __restrict__
     const size_t ck = e / nb;
     const int k = (int)(ck % nk), c = (int)(ck / nk);
     double2 ps = psi[e];
-    if (bco) {
-      const int v = c / na;
-      const double inv = v < MAXV ? sinv[v] : (active[v] ? 1.0 / bco[(size_t)v * stride + col] : 0.0);
+    if (f.norm_part) {
+      const double inv = sinv[c / na];
       if (inv != 0.0) {
         ps = make_double2(ps.x * inv, ps.y * inv);
         psi[e] = ps;
       }
     }
     const float re = (float)ps.x, im = (float)ps.y;
+    psi_f[e] = make_float2(re, im);
     __nv_bfloat16 h0, l0, h1, l1, h2, l2;
     split2(re, h0, l0);
     split2(-im, h1, l1);
@@ -460,10 +506,13 @@ __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
       im += sim[w];
     }
     f.partial[(size_t)v * gridDim.x + blockIdx.x] = make_double2(r, im);
-    __threadfence();
-    const unsigned prev = atomicAdd(f.counter, 1u);
-    last = prev == gridDim.x * gridDim.y - 1;
+    if (!f.deferred) {
+      __threadfence();
+      const unsigned prev = atomicAdd(f.counter, 1u);
+      last = prev == gridDim.x * gridDim.y - 1;
+    }
   }
+  if (f.deferred) return;
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -493,8 +542,9 @@ __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
 // core states, G of them per thread (NA / G threads per (k, n): more loads in
 // flight for this latency-bound pass); the projectors are read in FP32.
 template <int NA, int G>
-__global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ part, int nsplit,
-                                                    const double2* __restrict__ psi, double2* __restrict__ out,
+__global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict__ part, int nsplit,
+                                                    const double2* __restrict__ psi,
+                                                    const float2* __restrict__ psi_f, double2* __restrict__ out,
                                                     const double* __restrict__ e_nk, const double2* __restrict__ chi,
                                                     const float2* __restrict__ a_proj,
                                                     const double2* __restrict__ srcp, int nk, int nb, int np, int nc,
@@ -511,7 +561,7 @@ __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ p
   }
   for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) chs[i] = make_float2((float)chi[i].x, (float)chi[i].y);
   __syncthreads();
-  double dre = 0.0, dim = 0.0;
+  double dre = 0.0;
   const size_t total = nkb * NG;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t kn = e / NG;
@@ -519,10 +569,7 @@ __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ p
     const int k = (int)(kn / nb), n = (int)(kn % nb);
     float2 pf[NA];
 #pragma unroll
-    for (int b = 0; b < NA; ++b) {
-      const double2 d = psi[(size_t)(v * NA + b) * nkb + kn];
-      pf[b] = make_float2((float)d.x, (float)d.y);
-    }
+    for (int b = 0; b < NA; ++b) pf[b] = psi_f[(size_t)(v * NA + b) * nkb + kn];
     float2 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float2(0.f, 0.f);
@@ -565,11 +612,10 @@ __global__ void __launch_bounds__(256) g2b_final_na(const float2* __restrict__ p
       const double2 ps = psi[(size_t)c * nkb + kn];
       const double2 val = make_double2((double)rx + e_kn * ps.x, (double)ry + e_kn * ps.y);
       out[(size_t)c * nkb + kn] = val;
-      dre += ps.x * val.x + ps.y * val.y;
-      dim += ps.x * val.y - ps.y * val.x;
+      dre += ps.x * val.x + ps.y * val.y;   // Re <psi|H psi>: the only part the recursion uses
     }
   }
-  if (f.partial) fused_dot_tail(f, dre, dim);
+  if (f.partial) fused_dot_tail(f, dre, 0.0);
 }
 
 // out[c][k][n] = sum_split part + E psi - chi psi + short-range out.  Grid
@@ -733,6 +779,7 @@ bse_status bse_tc_prepare(bse_handle* h) {
   const size_t x64 = (size_t)(h->nx + TC_KB - 1) / TC_KB;
   const size_t nbf = (size_t)h->nk * x64 * ts->nnmax * TC_KB;   // K-tiled [k][x/64][row][64]
   if (cudaMalloc((void**)&h->bpsi, 2 * nbp * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc((void**)&h->psi_f, (size_t)h->max_vec * h->na * h->nk * h->nb * sizeof(float2)) != cudaSuccess ||
       cudaMalloc((void**)&h->bphi, 2 * nbf * sizeof(__nv_bfloat16)) != cudaSuccess ||
       cudaMalloc((void**)&h->part, (size_t)ts->smax * h->nk * h->nb * h->na * h->max_vec * sizeof(float2)) !=
           cudaSuccess ||
@@ -765,13 +812,14 @@ bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_d
   const int nc = n_vec * h->na;
   const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
   const size_t total = (size_t)nc * h->nk * h->nb;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)8 * ts->sms);
-  const bool scale = fuse && fuse->scale_b;
+  // two blocks per SM: each block of the lazy-normalisation form first reduces
+  // the update's |w|^2 partials in FP64 (slow pipe), so fewer blocks pay
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)2 * ts->sms);
+  bse_dotfuse f = (fuse && fuse->norm_part) ? *fuse : bse_dotfuse();
+  if (f.norm_part && n_vec > PREP_MAXV) return bse_fail(h, BSE_ERR_UNSUPPORTED, "lazy normalisation: too many vectors");
   BSE_PROF(h, BSE_K_PREP,
-           prep_bpsi<<<blocks, 256, 0, h->stream>>>(const_cast<double2*>(psi), h->bpsi, h->bpsi + nbp, h->nk, h->nb,
-                                                    nc, ts->kp, ts->nnmax, h->na, scale ? fuse->scale_b : nullptr,
-                                                    scale ? fuse->scale_col : 0, scale ? fuse->scale_stride : 0,
-                                                    scale ? fuse->active : nullptr));
+           prep_bpsi<<<blocks, 256, 0, h->stream>>>(const_cast<double2*>(psi), h->bpsi, h->bpsi + nbp, h->psi_f,
+                                                    h->nk, h->nb, nc, ts->kp, ts->nnmax, h->na, f));
   return bse_cuda_check(h, cudaGetLastError(), "prep_bpsi launch");
 }
 
@@ -836,27 +884,20 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   bse_status s = launch_gemm(h, ts, 1, ts->a6_hi, ts->a6_lo, b_hi, b_lo, p, BSE_K_GRID_TO_BAND);
   if (s != BSE_OK) return s;
   if (wait_side) cudaStreamWaitEvent(h->stream, h->ev_join, 0);   // short-range c' ready
-  const size_t per_vec = (size_t)h->na * h->nk * h->nb;
-  int blocks = (int)((per_vec + 255) / 256);
-  if (blocks > BSE_FINAL_BLOCKS) blocks = BSE_FINAL_BLOCKS;
+  const int blocks = bse_tc_final_blocks(h);
   bse_dotfuse f = fuse ? *fuse : bse_dotfuse();
-  const size_t nkb = (size_t)h->nk * h->nb;
-  auto final_grid = [&](int ng) {
-    int bk = (int)((nkb * ng + 255) / 256);
-    if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
-    return dim3((unsigned)bk, (unsigned)n_vec);
-  };
+  auto final_grid = [&](int) { return dim3((unsigned)blocks, (unsigned)n_vec); };
   const double2* srp = h->sr_cp;
   const float2* apf = h->a_proj_f;
   if (h->na == 6) {
     BSE_PROF(h, BSE_K_PREP,
-             (g2b_final_na<6, 1><<<final_grid(6), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi,
-                                                                       h->e_nk, h->chi, apf, srp, h->nk, h->nb,
+             (g2b_final_na<6, 1><<<final_grid(6), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, h->psi_f,
+                                                                       hpsi, h->e_nk, h->chi, apf, srp, h->nk, h->nb,
                                                                        h->np, nc, f)));
   } else if (h->na == 1) {
     BSE_PROF(h, BSE_K_PREP,
-             (g2b_final_na<1, 1><<<final_grid(1), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, hpsi,
-                                                                       h->e_nk, h->chi, apf, srp, h->nk, h->nb,
+             (g2b_final_na<1, 1><<<final_grid(1), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, h->psi_f,
+                                                                       hpsi, h->e_nk, h->chi, apf, srp, h->nk, h->nb,
                                                                        h->np, nc, f)));
   } else {
     BSE_PROF(h, BSE_K_PREP,
@@ -865,6 +906,20 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
                  h->na, h->np, nc, f));
   }
   return bse_cuda_check(h, cudaGetLastError(), "g2b_final launch");
+}
+
+int bse_tc_final_blocks(const bse_handle* h) {
+  const size_t nkb = (size_t)h->nk * h->nb;
+  // one thread per (k, n, alpha) of a vector up to two blocks per SM, grid-stride
+  // beyond: every block's <psi|H psi> partial is reduced again by each block of
+  // the Haydock update (FP64, a slow pipe on this part), so fewer partials pay
+  const size_t threads = nkb * (size_t)h->na;
+  size_t bk = (threads + 255) / 256;
+  const TcState* ts = (const TcState*)h->tmap_host;
+  const size_t cap = ts && ts->sms > 0 ? (size_t)2 * ts->sms : 304;
+  if (bk > cap) bk = cap;
+  if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
+  return (int)bk;
 }
 
 bse_status bse_tc_status(bse_handle* h) {

@@ -103,6 +103,36 @@ def test_haydock_on_capturable_stream_matches_oracle(prec):
         assert np.allclose(bc[v][:21], bo[:21], rtol=tol, atol=tol * 10)
 
 
+@pytest.mark.parametrize("capturable", [False, True])
+def test_haydock_split_bf16_breakdown_per_vector(capturable):
+    """Deferred reductions of the tensor-core Haydock loop: with W = 0, no
+    short-range term and chi = 0, H = diag(E) and H psi is exact, so a start
+    vector on three distinct energies breaks down after three steps while a
+    second, generic vector runs on; both equal the oracle's coefficients."""
+    torch = pytest.importorskip("torch")
+    s = S.tiny_system(71, n_alpha=1, nk=(2, 2, 2), n_bands=16, nx=(8, 8, 8), n_proj=0, w_const=0.0, so=False)
+    e = s.e_nk.reshape(-1)
+    b = np.zeros((2, s.dim), dtype=np.complex128)
+    idx = [3, 40, 77]
+    assert len(set(np.round(e[idx], 9))) == 3
+    b[0, idx] = [1.0, 0.5 - 0.5j, 0.25j]
+    b[1] = S.complex_normal(np.random.default_rng(9), (s.dim,))
+    stream = torch.cuda.Stream() if capturable else None
+    sysg = bse.System(s, precision="split_bf16", max_vec=2, stream=stream.cuda_stream if stream else None)
+    a, bc, steps, st = sysg.haydock(b, 8)
+    assert st == bse.BSE_ERR_BREAKDOWN
+    assert list(steps) == [3, 8]
+    ao, bo, nd, brk = O.haydock(lambda x: O.apply_h(s, x), b[0], 8)
+    assert nd == 3 and brk
+    assert np.allclose(a[0][:3], ao[:3], rtol=1e-12, atol=1e-12)
+    assert np.allclose(bc[0][:3], bo[:3], rtol=1e-12, atol=1e-12)
+    assert bc[0][3] <= 1e-12 * max(1.0, abs(a[0][2]))
+    ao, bo, nd, brk = O.haydock(lambda x: O.apply_h(s, x), b[1], 8)
+    assert nd == 8
+    assert np.allclose(a[1], ao, rtol=1e-10, atol=1e-10)
+    assert np.allclose(bc[1], bo, rtol=1e-10, atol=1e-10)
+
+
 def test_apply_h_device_pointers():
     torch = pytest.importorskip("torch")
     s = S.tiny_system(30, n_alpha=6, nk=(2, 2, 2), n_bands=12, nx=(6, 6, 6), n_proj=4)
