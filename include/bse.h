@@ -99,6 +99,10 @@ typedef struct {
 /* Copies the system to the device (current CUDA device), folds e^{ik.x} into
  * u, converts it to the requested precision and precomputes diag(H).
  * Sizes: 1 <= Na <= 16, 1 <= Nb <= Nx, nk_d in 1..16, Np in 0..64.
+ * Device-memory inputs are read on the handle's stream: work that produces
+ * them on another stream must be complete (or ordered before it) when
+ * bse_setup is called.  Returns after the set-up work has finished; the
+ * caller may then free or reuse its arrays.
  * On failure *out is NULL and nothing is leaked. */
 bse_status bse_setup(bse_handle** out, const bse_system_desc* desc);
 

@@ -193,13 +193,15 @@ def make_system(name: str = "k_edge_small", site: int = 0, *, overrides: dict | 
     return make_system_from(cfg, site=site, name=name)
 
 
-def make_system_from(cfg: dict, site: int = 0, name: str = "custom") -> BSESystem:
+def make_system_from(cfg: dict, site: int = 0, name: str = "custom", u=None) -> BSESystem:
+    """Draw one site of shape cfg; u_nk may be supplied (e.g. drawn on the GPU)."""
     cid = int(cfg.get("id", 99))
     nk = tuple(int(v) for v in cfg["nk"])
     nx = tuple(int(v) for v in cfg["nx"])
     n_k, n_x = int(np.prod(nk)), int(np.prod(nx))
     nb, na = int(cfg["n_bands"]), int(cfg["n_alpha"])
-    u = orthonormal_bloch(rng_for(cid, site, STREAM_U), n_k, n_x, nb)
+    if u is None:
+        u = orthonormal_bloch(rng_for(cid, site, STREAM_U), n_k, n_x, nb)
     e_nk = rng_for(cid, site, STREAM_E).uniform(0.0, 20.0, size=(n_k, nb))
     split = cfg.get("so_split")
     if na == 6 and split:
@@ -221,6 +223,58 @@ def make_system_from(cfg: dict, site: int = 0, name: str = "custom") -> BSESyste
     return BSESystem(n_alpha=na, nk=nk, n_bands=nb, nx=nx, cell=float(cfg["cell"]),
                      eps=float(cfg["eps"]), u=u, e_nk=e_nk, chi=chi, w_rx=w,
                      a_proj=a_proj, m_sr=m_sr, kshift=ks, name=name, meta=dict(cfg))
+
+
+def batched_site_config(site: int) -> dict:
+    """Shape of one site of the many-site workload: k mesh n^3 with
+    n ~ U{4..8}, grid m^3 with m ~ U{12..20}, Nb ~ U{32..256}, and 1 or 6 core
+    states with probability 1/2 each.  L-edge sites (6 core states) carry the
+    5.7 eV spin-orbit split and 36 local functions; 1s sites carry neither.
+    Cell 7.4 bohr, epsilon 5."""
+    r = rng_for(3, site, STREAM_SITE)
+    n = int(r.integers(4, 9))
+    m = int(r.integers(12, 21))
+    nb = int(r.integers(32, 257))
+    na = 6 if r.random() < 0.5 else 1
+    return dict(id=3, n_alpha=na, nk=(n, n, n), n_bands=nb, nx=(m, m, m), cell=7.4, eps=5.0,
+                n_proj=36 if na == 6 else 0, so_split=5.7 if na == 6 else None, m_scale=0.5)
+
+
+def orthonormal_bloch_device(seed: int, n_k: int, n_x: int, n_bands: int, device="cuda", chunk: int = 32):
+    """u_nk(x) drawn and orthonormalised on a GPU with torch, for workloads too
+    large to draw on the host: complex normal (Nx x Nb) per k from a seeded
+    torch generator, Householder QR (torch.linalg.qr), phases fixed so R has a
+    positive diagonal.  A different random stream from orthonormal_bloch;
+    returns a complex128 tensor [Nk][Nx][Nb] on the device, complete (the
+    device is synchronised) when the call returns."""
+    import torch
+    if n_bands > n_x:
+        raise ValueError("need n_bands <= n_x for orthonormal columns")
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    u = torch.empty((n_k, n_x, n_bands), dtype=torch.complex128, device=device)
+    for k0 in range(0, n_k, chunk):
+        k1 = min(n_k, k0 + chunk)
+        g = torch.randn((k1 - k0, n_x, n_bands), dtype=torch.complex128, device=device, generator=gen)
+        q, r = torch.linalg.qr(g)
+        d = torch.diagonal(r, dim1=-2, dim2=-1)
+        u[k0:k1] = q * (d / d.abs()).unsqueeze(-2)
+        del g, q, r, d
+    # the draw runs on torch's stream; consumers on other (non-blocking)
+    # streams must not see it half-written
+    torch.cuda.synchronize(device)
+    return u
+
+
+def make_system_device(cfg: dict, site: int = 0, name: str = "custom", device="cuda") -> BSESystem:
+    """make_system_from with u_nk from orthonormal_bloch_device (a torch
+    tensor on the device); every other array is drawn on the host as usual."""
+    cid = int(cfg.get("id", 99))
+    n_k = int(np.prod(cfg["nk"]))
+    n_x = int(np.prod(cfg["nx"]))
+    seed = (cid * 1000003 + int(site)) * 101 + STREAM_U
+    u = orthonormal_bloch_device(seed, n_k, n_x, int(cfg["n_bands"]), device=device)
+    return make_system_from(cfg, site=site, name=name, u=u)
 
 
 def make_start_vectors(sysd: BSESystem, n_vec: int = 1, seed: int = 0) -> np.ndarray:
