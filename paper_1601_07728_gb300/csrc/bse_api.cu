@@ -31,15 +31,26 @@ bse_status bse_cuda_check(bse_handle* h, cudaError_t e, const char* what) {
   return bse_fail(h, e == cudaErrorMemoryAllocation ? BSE_ERR_OOM : BSE_ERR_CUDA, m);
 }
 
+// Timing events around one launch.  Inside a stream capture they become
+// event-record nodes of the graph (external records), so a captured loop is
+// timed as it runs, back to back, rather than launch by launch.
+static void prof_record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 void bse_prof_begin(bse_handle* h, int kind) {
   if (!h->prof || h->ev_used + 2 > h->ev.size()) return;
-  cudaEventRecord(h->ev[h->ev_used], h->cur ? h->cur : h->stream);
+  prof_record(h->ev[h->ev_used], h->cur ? h->cur : h->stream);
   h->ev_kind[h->ev_used / 2] = kind;
 }
 
 void bse_prof_end(bse_handle* h) {
   if (!h->prof || h->ev_used + 2 > h->ev.size()) return;
-  cudaEventRecord(h->ev[h->ev_used + 1], h->cur ? h->cur : h->stream);
+  prof_record(h->ev[h->ev_used + 1], h->cur ? h->cur : h->stream);
   h->ev_used += 2;
 }
 

@@ -806,9 +806,9 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   }
   // The step loop is recorded into one CUDA graph and launched once (launch
   // gaps between the ~10 kernels of a step otherwise cost ~8 % of the step);
-  // without a capturable stream, or with per-launch profiling on, it runs
-  // eagerly.
-  const bool want_graph = allow_graph && !h->prof && h->stream != nullptr && !getenv("BSE_NO_GRAPH");
+  // without a capturable stream it runs eagerly.  Profiling events become
+  // event-record nodes of the graph.
+  const bool want_graph = allow_graph && h->stream != nullptr && !getenv("BSE_NO_GRAPH");
   bool capturing = false;
   if (want_graph) {
     capturing = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -818,7 +818,9 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   double2* const vc0 = vc;
   double2* const w0 = w;
   bse_status loop_status = BSE_OK;
+  const size_t ev_mark = h->ev_used;   // profiling events of a refused capture are recorded again
   for (int pass = 0; pass < 2; ++pass) {
+  h->ev_used = ev_mark;
   vp = vp0;
   vc = vc0;
   w = w0;
