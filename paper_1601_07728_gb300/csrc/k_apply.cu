@@ -160,36 +160,57 @@ __global__ void __launch_bounds__(256) g2b_simt(
 
 // ---------------------------------------------------------------------------
 // short range (Sec. 3.2.2): c[c][p] = sum_{kn} A[p][kn] psi[c][kn];  c' = M c
-// Split-K projection: block b sums kn in [b*SRK, (b+1)*SRK) for up to SRC
-// columns and all Np functions; part[b][c][p] (accumulated in T).
+// Split-K projection: block b sums kn in [b*SRK*srt, (b+1)*SRK*srt) in srt
+// shared-memory tiles of SRK for up to SRC columns and all Np functions,
+// accumulating in registers; part[b][c][p] (accumulated in T).  srt is as
+// large as keeps about two blocks per SM busy: longer blocks mean fewer
+// partials for the FP64 reduction (sr_reduce).
 // ---------------------------------------------------------------------------
-constexpr int SRK = 64, SRC = 16;
+constexpr int SRK = 64, SRC = 16, SRT_MAX = 8, SRO = 4;   // SRO: outputs per thread (SRC * Np <= 16 * 64 = 256 * SRO)
 template <typename T, typename AT, typename PT>
 __global__ void __launch_bounds__(256) sr_in_partial(const AT* __restrict__ a_proj,
                                                      const PT* __restrict__ psi,
-                                                     double2* __restrict__ part, int nkb, int np, int nc) {
+                                                     double2* __restrict__ part, int nkb, int np, int nc,
+                                                     int srt) {
   typedef typename Cx<T>::type C;
   extern __shared__ __align__(16) unsigned char sr_smem[];
   C* As = reinterpret_cast<C*>(sr_smem);   // [np][SRK + 1]
   C* Ps = As + (size_t)np * (SRK + 1);     // [SRC][SRK + 1]
   const int b = blockIdx.x, c0 = blockIdx.y * SRC;
   const int ncc = nc - c0 < SRC ? nc - c0 : SRC;
-  const int k0 = b * SRK;
-  for (int e = threadIdx.x; e < np * SRK; e += blockDim.x) {
-    const int p = e / SRK, i = e % SRK;
-    As[p * (SRK + 1) + i] = (k0 + i < nkb) ? from_d2<C>(a_proj[(size_t)p * nkb + k0 + i]) : czero<C>();
-  }
-  for (int e = threadIdx.x; e < ncc * SRK; e += blockDim.x) {
-    const int c = e / SRK, i = e % SRK;
-    Ps[c * (SRK + 1) + i] = (k0 + i < nkb) ? from_d2<C>(psi[(size_t)(c0 + c) * nkb + k0 + i]) : czero<C>();
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < ncc * np; o += blockDim.x) {
-    const int c = o / np, p = o % np;
-    C acc = czero<C>();
+  C acc[SRO];
+#pragma unroll
+  for (int r = 0; r < SRO; ++r) acc[r] = czero<C>();
+  for (int tile = 0; tile < srt; ++tile) {
+    const int k0 = (b * srt + tile) * SRK;
+    if (k0 >= nkb) break;   // uniform across the block
+    for (int e = threadIdx.x; e < np * SRK; e += blockDim.x) {
+      const int p = e / SRK, i = e % SRK;
+      As[p * (SRK + 1) + i] = (k0 + i < nkb) ? from_d2<C>(a_proj[(size_t)p * nkb + k0 + i]) : czero<C>();
+    }
+    for (int e = threadIdx.x; e < ncc * SRK; e += blockDim.x) {
+      const int c = e / SRK, i = e % SRK;
+      Ps[c * (SRK + 1) + i] = (k0 + i < nkb) ? from_d2<C>(psi[(size_t)(c0 + c) * nkb + k0 + i]) : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SRO; ++r) {
+      const int o = threadIdx.x + r * blockDim.x;
+      if (o < ncc * np) {
+        const int c = o / np, p = o % np;
 #pragma unroll 8
-    for (int i = 0; i < SRK; ++i) cmac(acc, As[p * (SRK + 1) + i], Ps[c * (SRK + 1) + i]);
-    part[((size_t)b * nc + c0 + c) * np + p] = make_double2((double)acc.x, (double)acc.y);
+        for (int i = 0; i < SRK; ++i) cmac(acc[r], As[p * (SRK + 1) + i], Ps[c * (SRK + 1) + i]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < SRO; ++r) {
+    const int o = threadIdx.x + r * blockDim.x;
+    if (o < ncc * np) {
+      const int c = o / np, p = o % np;
+      part[((size_t)b * nc + c0 + c) * np + p] = make_double2((double)acc[r].x, (double)acc[r].y);
+    }
   }
 }
 
@@ -266,7 +287,7 @@ bse_status apply_simt(bse_handle* h, const double2* psi, double2* hpsi, int n_ve
 }
 
 template <typename T>
-void launch_sr_in(bse_handle* h, const double2* psi, int nc, int nkb, int nblk) {
+void launch_sr_in(bse_handle* h, const double2* psi, int nc, int nkb, int nblk, int srt) {
   typedef typename Cx<T>::type C;
   dim3 g((unsigned)nblk, (unsigned)((nc + SRC - 1) / SRC));
   const size_t smem = (size_t)(h->np + SRC) * (SRK + 1) * sizeof(C);
@@ -275,17 +296,17 @@ void launch_sr_in(bse_handle* h, const double2* psi, int nc, int nkb, int nblk) 
     cudaFuncSetAttribute(sr_in_partial<T, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     BSE_PROF(h, BSE_K_SR_IN,
              (sr_in_partial<T, float2, float2><<<g, 256, smem, h->side>>>(h->a_proj_f, h->psi_f, h->sr_part, nkb,
-                                                                           h->np, nc)));
+                                                                           h->np, nc, srt)));
   } else if (h->a_proj_f) {   // FP32 form: FP32 copy of the projectors (half the bytes)
     cudaFuncSetAttribute(sr_in_partial<T, float2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     BSE_PROF(h, BSE_K_SR_IN,
              (sr_in_partial<T, float2, double2><<<g, 256, smem, h->side>>>(h->a_proj_f, psi, h->sr_part, nkb, h->np,
-                                                                            nc)));
+                                                                            nc, srt)));
   } else {
     cudaFuncSetAttribute(sr_in_partial<T, double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     BSE_PROF(h, BSE_K_SR_IN,
              (sr_in_partial<T, double2, double2><<<g, 256, smem, h->side>>>(h->a_proj, psi, h->sr_part, nkb, h->np,
-                                                                             nc)));
+                                                                             nc, srt)));
   }
 }
 
@@ -302,11 +323,15 @@ bse_status bse_sr_terms(bse_handle* h, const double2* psi, int n_vec) {
   h->cur = st;
   const int nc = n_vec * h->na;
   const int nkb = h->nk * h->nb;
-  const int nblk = (nkb + SRK - 1) / SRK;
+  const int tiles = (nkb + SRK - 1) / SRK;
+  const int cgroups = (nc + SRC - 1) / SRC;
+  int srt = tiles * cgroups / 304;   // keep >= ~2 blocks per SM of 152
+  srt = srt < 1 ? 1 : (srt > SRT_MAX ? SRT_MAX : srt);
+  const int nblk = (tiles + srt - 1) / srt;
   if (h->prec == BSE_PREC_FP64)
-    launch_sr_in<double>(h, psi, nc, nkb, nblk);
+    launch_sr_in<double>(h, psi, nc, nkb, nblk, srt);
   else
-    launch_sr_in<float>(h, psi, nc, nkb, nblk);
+    launch_sr_in<float>(h, psi, nc, nkb, nblk, srt);
   const int nout = nc * h->np;
   BSE_PROF(h, BSE_K_SR_IN, sr_reduce<<<nout, 128, 0, st>>>(h->sr_part, h->sr_c, nblk, nout));
   const int dimm = h->na * h->np;

@@ -235,6 +235,175 @@ __global__ void __launch_bounds__(256) kconv_cubic(typename CT<T>::t* __restrict
   }
 }
 
+// kconv_cubic2<N, BF16>: the FP32 transform of kconv_cubic with two
+// consecutive x per thread (even Nx): every shared-memory and global access
+// moves 16 bytes (two complex64), the bf16 planes are written as bf16 pairs,
+// so the memory and address instructions per point are halved while the
+// transform arithmetic is unchanged.  CTA: one column c and XC = 16
+// consecutive x (8 pairs); 256 threads = 8 pairs x 32 pencil groups.
+template <int N, bool BF16>
+__global__ void __launch_bounds__(256) kconv_cubic2(float2* __restrict__ phi, const float* __restrict__ w,
+                                                    const double* __restrict__ twiddle,
+                                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                                    int nx, int nc, int nnmax) {
+  constexpr int NK = N * N * N, NP = N * N;
+  constexpr int XP = XC / 2;                 // x pairs per CTA
+  constexpr int NG = 256 / XP;               // pencil groups (32)
+  constexpr int PPT = (NP + NG - 1) / NG;    // pencils per thread
+  extern __shared__ __align__(16) unsigned char kc_smem[];
+  float4* S = reinterpret_cast<float4*>(kc_smem);   // [NK][XP], each entry (x, x+1)
+  const int xp = threadIdx.x & (XP - 1), g = threadIdx.x / XP;
+  const int c = blockIdx.y, x = blockIdx.x * XC + 2 * xp;
+  const bool xin = x < nx;                   // Nx even: then x + 1 < Nx as well
+  float2 tw[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    tw[j].x = (float)twiddle[2 * j];
+    tw[j].y = (float)twiddle[2 * j + 1];
+  }
+  const size_t colstride = (size_t)nc * nx;
+  float2* base = phi + (size_t)c * nx + x;
+  // pass A: global load + forward transform along axis 2
+  {
+    float2 va[PPT][N], vb[PPT][N];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int p = g + NG * i;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (xin && p < NP) q = *reinterpret_cast<const float4*>(base + (size_t)(p * N + j) * colstride);
+        va[i][j] = make_float2(q.x, q.y);
+        vb[i][j] = make_float2(q.z, q.w);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int p = g + NG * i;
+      if (p < NP) {
+        dftN<float, N, +1>(va[i], tw);
+        dftN<float, N, +1>(vb[i], tw);
+#pragma unroll
+        for (int j = 0; j < N; ++j) S[(p * N + j) * XP + xp] = make_float4(va[i][j].x, va[i][j].y, vb[i][j].x, vb[i][j].y);
+      }
+    }
+  }
+  __syncthreads();
+  // pass B: forward along axis 1; pencil p = (m0, m2): k = m0 N^2 + j N + m2
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + NG * i;
+    if (p < NP) {
+      const int kb = (p / N) * NP + (p % N);
+      float2 va[N], vb[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float4 q = S[(kb + j * N) * XP + xp];
+        va[j] = make_float2(q.x, q.y);
+        vb[j] = make_float2(q.z, q.w);
+      }
+      dftN<float, N, +1>(va, tw);
+      dftN<float, N, +1>(vb, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[(kb + j * N) * XP + xp] = make_float4(va[j].x, va[j].y, vb[j].x, vb[j].y);
+    }
+  }
+  __syncthreads();
+  // pass C: forward along axis 0, times W(x, R)/Nk, inverse along axis 0; p = (m1, m2): k = j N^2 + p
+  const float inv = 1.f / (float)NK;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + NG * i;
+    if (p < NP) {
+      float2 wr[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        wr[j] = xin ? *reinterpret_cast<const float2*>(w + (size_t)(j * NP + p) * nx + x) : make_float2(0.f, 0.f);
+        wr[j].x *= inv;
+        wr[j].y *= inv;
+      }
+      float2 va[N], vb[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float4 q = S[(j * NP + p) * XP + xp];
+        va[j] = make_float2(q.x, q.y);
+        vb[j] = make_float2(q.z, q.w);
+      }
+      dftN<float, N, +1>(va, tw);
+      dftN<float, N, +1>(vb, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        va[j].x *= wr[j].x;
+        va[j].y *= wr[j].x;
+        vb[j].x *= wr[j].y;
+        vb[j].y *= wr[j].y;
+      }
+      dftN<float, N, -1>(va, tw);
+      dftN<float, N, -1>(vb, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[(j * NP + p) * XP + xp] = make_float4(va[j].x, va[j].y, vb[j].x, vb[j].y);
+    }
+  }
+  __syncthreads();
+  // pass D: inverse along axis 1
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + NG * i;
+    if (p < NP) {
+      const int kb = (p / N) * NP + (p % N);
+      float2 va[N], vb[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float4 q = S[(kb + j * N) * XP + xp];
+        va[j] = make_float2(q.x, q.y);
+        vb[j] = make_float2(q.z, q.w);
+      }
+      dftN<float, N, -1>(va, tw);
+      dftN<float, N, -1>(vb, tw);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[(kb + j * N) * XP + xp] = make_float4(va[j].x, va[j].y, vb[j].x, vb[j].y);
+    }
+  }
+  __syncthreads();
+  // pass E: inverse along axis 2 + store
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int p = g + NG * i;
+    if (p < NP) {
+      float2 va[N], vb[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float4 q = S[(p * N + j) * XP + xp];
+        va[j] = make_float2(q.x, q.y);
+        vb[j] = make_float2(q.z, q.w);
+      }
+      dftN<float, N, -1>(va, tw);
+      dftN<float, N, -1>(vb, tw);
+      if (xin) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int k = p * N + j;
+          if constexpr (BF16) {
+            // K-tiled planes [k][x/64][row][64], rows 2c (re) and 2c+1 (im); x, x+1 in one 64-block
+            const size_t o = (((size_t)k * ((nx + 63) >> 6) + (x >> 6)) * nnmax + 2 * c) * 64 + (x & 63);
+            __nv_bfloat16 h0, l0, h1, l1, h2, l2, h3, l3;
+            split_bf(va[j].x, h0, l0);
+            split_bf(vb[j].x, h1, l1);
+            split_bf(va[j].y, h2, l2);
+            split_bf(vb[j].y, h3, l3);
+            *reinterpret_cast<__nv_bfloat162*>(hi + o) = __halves2bfloat162(h0, h1);
+            *reinterpret_cast<__nv_bfloat162*>(lo + o) = __halves2bfloat162(l0, l1);
+            *reinterpret_cast<__nv_bfloat162*>(hi + o + 64) = __halves2bfloat162(h2, h3);
+            *reinterpret_cast<__nv_bfloat162*>(lo + o + 64) = __halves2bfloat162(l2, l3);
+          } else {
+            *reinterpret_cast<float4*>(base + (size_t)k * colstride) = make_float4(va[j].x, va[j].y, vb[j].x, vb[j].y);
+          }
+        }
+      }
+    }
+  }
+}
+
 // Generic mesh: one shared-memory pass per axis with explicit sums; CTA owns
 // XC consecutive x of one column c.  S[k][xl].
 template <typename T, int SIGN>
@@ -339,6 +508,15 @@ void launch_cubic(bse_handle* h, dim3 g, typename CT<T>::t* phi, const T* w, __n
            kconv_cubic<T, N, BF16><<<g, 256, smem, h->stream>>>(phi, w, h->twiddle, hi, lo, h->nx, nc, nnmax));
 }
 
+template <int N, bool BF16>
+void launch_cubic2(bse_handle* h, dim3 g, float2* phi, const float* w, __nv_bfloat16* hi, __nv_bfloat16* lo, int nc,
+                   int nnmax) {
+  const size_t smem = (size_t)N * N * N * XC * sizeof(float2);
+  cudaFuncSetAttribute(kconv_cubic2<N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  BSE_PROF(h, BSE_K_KCONV,
+           kconv_cubic2<N, BF16><<<g, 256, smem, h->stream>>>(phi, w, h->twiddle, hi, lo, h->nx, nc, nnmax));
+}
+
 template <typename T, bool BF16>
 bse_status launch(bse_handle* h, int nc, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax) {
   typedef typename CT<T>::t C;
@@ -346,6 +524,16 @@ bse_status launch(bse_handle* h, int nc, __nv_bfloat16* hi, __nv_bfloat16* lo, i
   const T* w = (const T*)h->w;
   const dim3 g((unsigned)((h->nx + XC - 1) / XC), (unsigned)nc);
   const int n = h->nk3[0];
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (h->nk3[1] == n && h->nk3[2] == n && (n == 4 || n == 8) && h->nx % 2 == 0) {
+      // FP32, even Nx: two x per thread
+      if (n == 8)
+        launch_cubic2<8, BF16>(h, g, (float2*)phi, (const float*)w, hi, lo, nc, nnmax);
+      else
+        launch_cubic2<4, BF16>(h, g, (float2*)phi, (const float*)w, hi, lo, nc, nnmax);
+      return bse_cuda_check(h, cudaGetLastError(), "k-transform launch");
+    }
+  }
   if (h->nk3[1] == n && h->nk3[2] == n && n <= 8) {
 #define KCUBIC(NN)                                                  \
   case NN:                                                          \

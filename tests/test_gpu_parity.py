@@ -69,6 +69,22 @@ def test_apply_h_split_bf16_matches_oracle(kw):
         assert rel(out[v], ref[v]) < TOL["split_bf16"]
 
 
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
+def test_cubic_k_meshes_match_oracle(n, prec):
+    """Every cubic k mesh 3^3..8^3 through the register-pencil k-transforms, on
+    an even grid (FP32 forms: two grid points per thread) and an odd one."""
+    for nx in ((4, 4, 4), (5, 3, 3)):
+        s = S.tiny_system(80 + n, n_alpha=6, nk=(n, n, n), n_bands=12, nx=nx, n_proj=3)
+        psi = S.complex_normal(np.random.default_rng(n), (2, s.dim))
+        sysg = bse.System(s, precision=prec, max_vec=2)
+        out = sysg.apply_h(psi)
+        sysg.close()
+        ref = O.apply_h(s, psi)
+        for v in range(2):
+            assert rel(out[v], ref[v]) < TOL[prec], (nx, v)
+
+
 @pytest.mark.parametrize("max_vec", [3, 2])
 def test_haydock_batched_vectors_split_bf16(max_vec):
     """Three start vectors (polarisations) in one Haydock call: fused epilogue
