@@ -159,7 +159,23 @@ struct bse_dotfuse {
   double* bco = nullptr;
   int* active_rw = nullptr;
   int* steps = nullptr;
+  // operand_ready (tensor-core form, N_alpha in {1, 6}): the previous Haydock
+  // update already wrote the band->grid operand and the FP32 copy of psi = w_i
+  // unnormalised, so the operand pass is skipped and the grid->band epilogue
+  // does the lazy normalisation (every term it adds is linear in psi)
+  bool operand_ready = false;
 };
+
+// Where a Haydock update writes the next step's band->grid operand (bf16
+// hi/lo [Nk][Nrow][K_p]) and FP32 psi; hi == nullptr: not written.
+struct bse_operand_out {
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;
+  float2* psi_f = nullptr;
+  int nk = 0, nb = 0, na = 0, kp = 0, nnmax = 0;
+};
+// the tensor-core form's operand buffers of a handle (k_tc.cu)
+bse_operand_out bse_tc_operand(const bse_handle* h);
 
 // H psi on device pointers (k_apply.cu); psi/hpsi [n_vec][N] double2, n_vec <= max_vec.
 // With fuse != nullptr the tensor-core form also produces a_i (returns

@@ -360,8 +360,10 @@ bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, in
     case BSE_PREC_SPLIT_BF16: {
       // the operand pass runs first: it may rescale psi in place (lazy Haydock
       // normalisation), and the short-range side stream forks after it
-      s = bse_tc_prep(h, psi, n_vec, fuse);
-      if (s != BSE_OK) return s;
+      if (!(fuse && fuse->operand_ready)) {
+        s = bse_tc_prep(h, psi, n_vec, fuse);
+        if (s != BSE_OK) return s;
+      }
       s = bse_sr_terms(h, psi, n_vec);
       if (s != BSE_OK) return s;
       s = bse_tc_band_to_grid(h, n_vec);

@@ -664,12 +664,22 @@ __device__ double block_sum_x_k(const double2* __restrict__ part, int n) {
 // block reduces the epilogue's partials of <v_i|H v_i> to a_i itself (block 0
 // records it), applies w -= a_i v_i + b_i v_{i-1}, and writes its partial of
 // |w|^2, which the next step's operand pass (or hay_norm_final) reduces.
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// With op.hi set the update also writes the next step's band->grid operand
+// from w_{i+1} (unnormalised): bf16 hi/lo rows 2c (Re: psi_r, -psi_i) and 2c+1
+// (Im: psi_i, psi_r) at columns 2n, 2n+1, and the FP32 copy of w_{i+1}; the
+// next step's epilogue applies 1/b_{i+1}.
 __global__ void __launch_bounds__(RB) hay_update_deferred(double2* __restrict__ w, const double2* __restrict__ vc,
                                                           const double2* __restrict__ vp, long long N,
                                                           const double2* __restrict__ fpart, int nfb,
                                                           double* __restrict__ a, const double* __restrict__ bco,
                                                           int n_steps, int i, const int* __restrict__ active,
-                                                          double2* __restrict__ partial, int* status) {
+                                                          double2* __restrict__ partial, int* status,
+                                                          bse_operand_out op) {
   const int v = blockIdx.y;
   if (!active[v]) {
     if (threadIdx.x == 0) partial[(size_t)v * gridDim.x + blockIdx.x] = make_double2(0.0, 0.0);
@@ -695,6 +705,24 @@ __global__ void __launch_bounds__(RB) hay_update_deferred(double2* __restrict__ 
     }
     w[o] = ww;
     acc += ww.x * ww.x + ww.y * ww.y;
+    if (op.hi) {
+      const float re = (float)ww.x, im = (float)ww.y;
+      op.psi_f[o] = make_float2(re, im);
+      const int n = (int)(e % op.nb);
+      const long long ak = e / op.nb;
+      const int k = (int)(ak % op.nk);
+      const int cc = v * op.na + (int)(ak / op.nk);
+      __nv_bfloat16 h0, l0, h1, l1, h2, l2;
+      split_bf16(re, h0, l0);
+      split_bf16(-im, h1, l1);
+      split_bf16(im, h2, l2);
+      const size_t o0 = ((size_t)k * op.nnmax + 2 * cc) * op.kp + 2 * n;
+      const size_t o1 = o0 + op.kp;
+      *reinterpret_cast<__nv_bfloat162*>(op.hi + o0) = __halves2bfloat162(h0, h1);
+      *reinterpret_cast<__nv_bfloat162*>(op.lo + o0) = __halves2bfloat162(l0, l1);
+      *reinterpret_cast<__nv_bfloat162*>(op.hi + o1) = __halves2bfloat162(h2, h0);
+      *reinterpret_cast<__nv_bfloat162*>(op.lo + o1) = __halves2bfloat162(l2, l0);
+    }
   }
   __shared__ double ws[RB / 32];
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -779,6 +807,10 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   // are reduced by their consumers (the update kernel, the next operand pass),
   // and v_{i+1} = w / b_{i+1} is applied in place by the next operand pass
   const bool lazy_scale = fuse_a && fuse_b && n_vec <= 64;
+  // ... and for N_alpha in {1, 6} the update writes the next operand itself
+  // (the operand pass disappears from steps >= 1)
+  const bool fused_op = lazy_scale && (h->na == 1 || h->na == 6);
+  const bse_operand_out opd = fused_op ? bse_tc_operand(h) : bse_operand_out();
   const int ublk = (int)std::min<long long>(UBLK, (N + RB - 1) / RB);
   const int nfb = fuse_a ? bse_tc_final_blocks(h) : 0;
   if (reorth) {
@@ -843,6 +875,7 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
           f.bco = b_d;
           f.active_rw = active;
           f.steps = steps_d;
+          f.operand_ready = fused_op;
         }
       }
       loop_status = bse_apply_device(h, vc, w, n_vec, &f);     // w = H v_i, a_i = Re <v_i|w>
@@ -855,8 +888,9 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
     }
     if (lazy_scale) {
       BSE_PROF(h, BSE_K_RECURSION,
-               hay_update_deferred<<<dim3(ublk, n_vec), RB, 0, st>>>(w, vc, vp, N, fpart, nfb, a_d, b_d, n_steps, i,
-                                                                     active, hpart, status));
+               hay_update_deferred<<<dim3(ublk, n_vec), RB, 0, st>>>(
+                   w, vc, vp, N, fpart, nfb, a_d, b_d, n_steps, i, active, hpart, status,
+                   i + 1 < n_steps ? opd : bse_operand_out()));
     } else if (fuse_b) {
       BSE_PROF(h, BSE_K_RECURSION,
                hay_update_fin<<<dim3(ublk, n_vec), RB, 0, st>>>(

@@ -543,7 +543,7 @@ __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
 // flight for this latency-bound pass); the projectors are read in FP32.
 template <int NA, int G>
 __global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict__ part, int nsplit,
-                                                    const double2* __restrict__ psi,
+                                                    double2* __restrict__ psi,
                                                     const float2* __restrict__ psi_f, double2* __restrict__ out,
                                                     const double* __restrict__ e_nk, const double2* __restrict__ chi,
                                                     const float2* __restrict__ a_proj,
@@ -561,6 +561,39 @@ __global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict_
   }
   for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) chs[i] = make_float2((float)chi[i].x, (float)chi[i].y);
   __syncthreads();
+  // lazy normalisation (operand written by the previous update from w_i): every
+  // block reduces |w_i|^2 in the same order; block 0 records b_i, the step count
+  // and the breakdown test; the linear terms are scaled by 1/b_i and psi is
+  // normalised in place (each element by the one thread that owns it)
+  const bool lazy = f.operand_ready && f.norm_part;
+  double inv = 1.0;
+  if (lazy) {
+    const double s = block_sum_x(f.norm_part + (size_t)v * f.norm_n, f.norm_n);
+    __shared__ double sinv;
+    if (threadIdx.x == 0) {
+      double iv = 0.0;
+      if (f.active_rw[v]) {
+        const double bn = sqrt(s);
+        const double ai = f.a[(size_t)v * f.a_stride + f.i - 1];
+        int st = 0;
+        if (!isfinite(bn) || !isfinite(ai)) st = 2;
+        else if (bn <= 1e-12 * fmax(1.0, fabs(ai))) st = 1;
+        if (blockIdx.x == 0) {
+          f.bco[(size_t)v * (f.a_stride + 1) + f.i] = bn;
+          f.steps[v] = f.i;
+          if (st) {
+            f.active_rw[v] = 0;
+            atomicOr(f.status, st);
+          }
+        }
+        if (!st) iv = 1.0 / bn;
+      }
+      sinv = iv;
+    }
+    __syncthreads();
+    inv = sinv;
+  }
+  const float finv = (float)inv;
   double dre = 0.0;
   const size_t total = nkb * NG;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -609,7 +642,13 @@ __global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict_
         rx += t.x;
         ry += t.y;
       }
-      const double2 ps = psi[(size_t)c * nkb + kn];
+      double2 ps = psi[(size_t)c * nkb + kn];
+      if (lazy) {
+        rx *= finv;
+        ry *= finv;
+        ps = make_double2(ps.x * inv, ps.y * inv);
+        if (inv != 0.0) psi[(size_t)c * nkb + kn] = ps;
+      }
       const double2 val = make_double2((double)rx + e_kn * ps.x, (double)ry + e_kn * ps.y);
       out[(size_t)c * nkb + kn] = val;
       dre += ps.x * val.x + ps.y * val.y;   // Re <psi|H psi>: the only part the recursion uses
@@ -891,12 +930,14 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   const float2* apf = h->a_proj_f;
   if (h->na == 6) {
     BSE_PROF(h, BSE_K_PREP,
-             (g2b_final_na<6, 1><<<final_grid(6), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, h->psi_f,
+             (g2b_final_na<6, 1><<<final_grid(6), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit,
+                                                                       const_cast<double2*>(psi), h->psi_f,
                                                                        hpsi, h->e_nk, h->chi, apf, srp, h->nk, h->nb,
                                                                        h->np, nc, f)));
   } else if (h->na == 1) {
     BSE_PROF(h, BSE_K_PREP,
-             (g2b_final_na<1, 1><<<final_grid(1), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit, psi, h->psi_f,
+             (g2b_final_na<1, 1><<<final_grid(1), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit,
+                                                                       const_cast<double2*>(psi), h->psi_f,
                                                                        hpsi, h->e_nk, h->chi, apf, srp, h->nk, h->nb,
                                                                        h->np, nc, f)));
   } else {
@@ -906,6 +947,22 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
                  h->na, h->np, nc, f));
   }
   return bse_cuda_check(h, cudaGetLastError(), "g2b_final launch");
+}
+
+bse_operand_out bse_tc_operand(const bse_handle* h) {
+  bse_operand_out o;
+  const TcState* ts = (const TcState*)h->tmap_host;
+  if (!ts || h->prec != BSE_PREC_SPLIT_BF16) return o;
+  const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
+  o.hi = h->bpsi;
+  o.lo = h->bpsi + nbp;
+  o.psi_f = h->psi_f;
+  o.nk = h->nk;
+  o.nb = h->nb;
+  o.na = h->na;
+  o.kp = ts->kp;
+  o.nnmax = ts->nnmax;
+  return o;
 }
 
 int bse_tc_final_blocks(const bse_handle* h) {
