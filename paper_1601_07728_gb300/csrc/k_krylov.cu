@@ -159,23 +159,6 @@ __global__ void __launch_bounds__(RB) hay_b_finalize(const double2* partial, int
   }
 }
 
-// h[v][j] partials: <basis[v][j] | w[v]>, grid (nblk, nj, nv)
-__global__ void __launch_bounds__(RB) gs_dot_partial(const double2* __restrict__ basis, long long bstride,
-                                                     const double2* __restrict__ w, long long N,
-                                                     double2* __restrict__ partial) {
-  const int j = blockIdx.y, v = blockIdx.z;
-  const double2* bv = basis + (size_t)v * bstride + (size_t)j * N;
-  const double2* wv = w + (size_t)v * N;
-  double2 acc = make_double2(0, 0);
-  for (long long e = (long long)blockIdx.x * RB + threadIdx.x; e < N; e += (long long)gridDim.x * RB) {
-    double2 a = bv[e], b = wv[e];
-    acc.x += a.x * b.x + a.y * b.y;
-    acc.y += a.x * b.y - a.y * b.x;
-  }
-  double2 s = block_sum2(acc);
-  if (threadIdx.x == 0) partial[((size_t)v * gridDim.y + j) * gridDim.x + blockIdx.x] = s;
-}
-
 // coef[v][j] = sum of partials (grid (nj, nv)); optionally accumulated into hacc
 __global__ void __launch_bounds__(RB) gs_dot_finalize(const double2* partial, int nblk, double2* coef,
                                                       int coef_stride, double2* hacc, int hacc_stride) {
@@ -407,20 +390,6 @@ __global__ void __launch_bounds__(RB) gm_beta(const double2* partial, int nblk, 
   }
 }
 
-// T = P V_j (Jacobi: P = 1/(d - z); none: identity)
-__global__ void gm_precond(const double2* __restrict__ V, long long vstride, double2* __restrict__ T,
-                           long long N, const double* __restrict__ d, const double2* __restrict__ z,
-                           int jacobi) {
-  const int v = blockIdx.y;
-  const double2 zv = z[v];
-  const double2* vv = V + (size_t)v * vstride;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-    double2 a = vv[e];
-    if (jacobi) a = cdiv(a, make_double2(d[e] - zv.x, -zv.y));
-    T[(size_t)v * N + e] = a;
-  }
-}
-
 // compact form for the still-active systems: slot s holds system idx[s]
 // T[s] = P V_j[idx[s]]
 __global__ void gm_precond_c(const double2* __restrict__ V, long long vstride, double2* __restrict__ T, long long N,
@@ -445,18 +414,6 @@ __global__ void gm_scatter_shift(const double2* __restrict__ Wc, const double2* 
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
     const double2 t = T[(size_t)s * N + e], w = Wc[(size_t)s * N + e];
     W[(size_t)v * N + e] = make_double2(w.x - (zv.x * t.x - zv.y * t.y), w.y - (zv.x * t.y + zv.y * t.x));
-  }
-}
-
-// W -= z T
-__global__ void gm_shift(double2* __restrict__ W, const double2* __restrict__ T, const double2* __restrict__ z,
-                         long long N) {
-  const int v = blockIdx.y;
-  const double2 zv = z[v];
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-    size_t o = (size_t)v * N + e;
-    double2 t = T[o], w = W[o];
-    W[o] = make_double2(w.x - (zv.x * t.x - zv.y * t.y), w.y - (zv.x * t.y + zv.y * t.x));
   }
 }
 
