@@ -227,6 +227,7 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     sysg = bse.System(s, precision=args.precision, max_vec=1, stream=stream.cuda_stream)
+    tiles = sysg.autotune(n_vec=1, reps=5)   # timed tile search (split-K, pipeline stages), before any timing
     n = sysg.dim
     db = torch.from_numpy(b).to("cuda")
     K, W = args.steps, args.warmup
@@ -311,6 +312,7 @@ def main():
     if args.polarisations > 1:
         npol = args.polarisations
         sys3 = bse.System(s, precision=args.precision, max_vec=npol, stream=stream.cuda_stream)
+        sys3.autotune(n_vec=npol, reps=5)
         b3 = torch.from_numpy(S.make_start_vectors(s, npol)).to("cuda")
         a3 = torch.zeros((npol, K), dtype=torch.float64, device="cuda")
         bb3 = torch.zeros((npol, K + 1), dtype=torch.float64, device="cuda")
@@ -346,6 +348,7 @@ def main():
         n_om = args.gmres_omega
         zs = np.linspace(-5.0, 30.0, n_om) + 0.5j
         sys_g = bse.System(s, precision=args.precision, max_vec=args.gmres_chunk, stream=stream.cuda_stream)
+        sys_g.autotune(n_vec=args.gmres_chunk, reps=3)
         xg = torch.empty((n_om, n), dtype=torch.complex128, device="cuda")
         sys_g.gmres(db, zs[:2], rtol=1e-3, restart=30, max_iter=60, precond="none", x=xg[:2])   # warm-up
         gm = {"n_omega": n_om, "rtol": 1e-6, "restart": 30, "max_iter": args.gmres_max_iter,
@@ -461,7 +464,9 @@ def main():
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "precision": args.precision,
                        "recursion": "f64 Haydock, no re-orthogonalisation", "n_vec": 1, "dim": n,
-                       "l2": "inputs larger than L2 (u_nk 1.07 GB), no flush", "parallelism": "replicas"},
+                       "l2": "inputs larger than L2 (u_nk 1.07 GB), no flush", "parallelism": "replicas",
+                       "tiles": {"grid_to_band_split_k": tiles[0], "pipeline_stages": tiles[1],
+                                 "chosen_by": "bse_autotune timed search"}},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                          "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3, "launches": nl},

@@ -283,6 +283,18 @@ typedef enum {
   BSE_K_COUNT = 7
 } bse_kernel_kind;
 
+/* Tile search for the tensor-core form (no counterpart in the paper): times
+ * H psi on n_vec (<= max_vec) internal test vectors, reps applications per
+ * candidate, for every grid->band split-K factor in {1, 2, 4, 8, 16} (at most
+ * one per 64-point K block of the grid) and every pipeline depth in
+ * {3, 4, 6, 8} stages that fits shared memory, and keeps the fastest pair for
+ * the handle (split_out, stages_out: host, may be NULL).  The choice changes
+ * only the order of the FP32 partial sums of grid->band.  Other precisions:
+ * no-op, outputs 0.  Allocates its test vectors (and a larger partial-sum
+ * buffer when needed) and synchronises the handle's stream, so call it
+ * outside any stream capture, e.g. right after bse_setup. */
+bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* split_out, int* stages_out);
+
 /* Measurement aid, no counterpart in the paper: when enabled, every kernel
  * launch of the handle is bracketed by CUDA events on the handle's stream
  * (a pool of 8192 launches; later launches are not timed).  bse_profile_read

@@ -764,26 +764,34 @@ bool make_map_tiled(CUtensorMap* m, const void* base, uint64_t rows, uint64_t ro
 
 struct TcState {
   int kp = 0, nnmax = 0, smax = 0, sms = 0;
+  int stages = 0;       // pipeline stages (0: chosen by rule per tile width)
+  int part_cap = 0;     // split-K factor the partial buffer is sized for
   int* err = nullptr;   // device error word
   CUtensorMap a2_hi, a2_lo, a6_hi, a6_lo;
 };
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-int pick_stages(int nn) {
+// most pipeline stages that fit shared memory for MMA width nn (at most 8)
+int fit_stages(int nn) {
   const int stage = 2 * TC_M * 128 + 2 * nn * 128;
   int s = (SMEM_BUDGET - 1024 - 256) / stage;
-  if (s > 8) s = 8;
-  // narrow (HBM-bound) tiles: four stages (~150 KB) keep ~25 MB in flight over
-  // the GPU, and leave shared memory for the short-range kernels of the side
-  // stream to run on the same SMs during the GEMM
+  return s > 8 ? 8 : s;
+}
+
+int pick_stages(int nn, int tuned) {
+  int s = fit_stages(nn);
+  if (tuned > 0) return tuned < s ? tuned : s;
+  // rule: narrow (HBM-bound) tiles get four stages (~150 KB), which keep ~25 MB
+  // in flight over the GPU and leave shared memory for the short-range kernels
+  // of the side stream to run on the same SMs during the GEMM
   if (nn <= 32 && s > 4) s = 4;
   return s;
 }
 
 bse_status launch_gemm(bse_handle* h, TcState* ts, int mode, const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                        const CUtensorMap& b_hi, const CUtensorMap& b_lo, TcParams p, int kind) {
-  p.stages = pick_stages(p.nn);
+  p.stages = pick_stages(p.nn, ts->stages);
   if (p.stages < 2) return bse_fail(h, BSE_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
   uint32_t cols = 32;
   while (cols < (uint32_t)(2 * p.nn)) cols <<= 1;
@@ -814,6 +822,7 @@ bse_status bse_tc_prepare(bse_handle* h) {
   int sp = 1;
   while (units * sp < 8 * ts->sms && kbt / (sp * 2) >= 8) sp *= 2;
   ts->smax = sp;
+  ts->part_cap = sp;
   const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
   const size_t x64 = (size_t)(h->nx + TC_KB - 1) / TC_KB;
   const size_t nbf = (size_t)h->nk * x64 * ts->nnmax * TC_KB;   // K-tiled [k][x/64][row][64]
@@ -977,6 +986,95 @@ int bse_tc_final_blocks(const bse_handle* h) {
   if (bk > cap) bk = cap;
   if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
   return (int)bk;
+}
+
+// Timed search over the tensor-core tile parameters of one handle (see
+// bse_autotune in bse.h).
+extern "C" bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* split_out, int* stages_out) {
+  if (!h) return BSE_ERR_INVALID_ARG;
+  if (n_vec < 1 || n_vec > h->max_vec || reps < 1)
+    return bse_fail(h, BSE_ERR_INVALID_ARG, "autotune: need 1 <= n_vec <= max_vec and reps >= 1");
+  if (h->prec != BSE_PREC_SPLIT_BF16 || !h->tmap_host) {
+    if (split_out) *split_out = 0;
+    if (stages_out) *stages_out = 0;
+    return BSE_OK;
+  }
+  TcState* ts = (TcState*)h->tmap_host;
+  cudaStream_t st = h->stream;
+  {
+    const bse_status ss = bse_cuda_check(h, cudaStreamSynchronize(st), "autotune sync");
+    if (ss != BSE_OK) return ss;
+  }
+  const int kbt = (h->nx + TC_KB - 1) / TC_KB;
+  std::vector<int> splits;
+  for (int s = 1; s <= 16 && s <= kbt; s *= 2) splits.push_back(s);
+  const int nn = round_up(2 * n_vec * h->na, 16);
+  const int fit = fit_stages(nn);
+  std::vector<int> stages;
+  for (int s : {3, 4, 6, 8})
+    if (s <= fit) stages.push_back(s);
+  if (stages.empty()) stages.push_back(fit);
+  if (splits.back() > ts->part_cap) {   // partial sums for the largest split-K factor tried
+    float2* np = nullptr;
+    if (cudaMalloc((void**)&np, (size_t)splits.back() * h->nk * h->nb * h->na * h->max_vec * sizeof(float2)) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return bse_fail(h, BSE_ERR_OOM, "autotune: partial-sum buffer");
+    }
+    cudaFree(h->part);
+    h->part = (float*)np;
+    ts->part_cap = splits.back();
+  }
+  double2 *psi = nullptr, *hpsi = nullptr;
+  const size_t bytes = (size_t)n_vec * h->N * sizeof(double2);
+  if (cudaMalloc((void**)&psi, bytes) != cudaSuccess || cudaMalloc((void**)&hpsi, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(psi);
+    return bse_fail(h, BSE_ERR_OOM, "autotune: test vectors");
+  }
+  cudaMemsetAsync(psi, 0x3f, bytes, st);   // finite test values (~4.8e-4); the timing does not depend on them
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int keep_split = ts->smax, keep_stages = ts->stages;
+  int best_split = keep_split, best_stages = keep_stages;
+  float best = 3.4e38f;
+  bse_status s = BSE_OK;
+  for (int sp : splits) {
+    for (int sg : stages) {
+      ts->smax = sp;
+      ts->stages = sg;
+      s = bse_apply_device(h, psi, hpsi, n_vec);   // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && s == BSE_OK; ++r) s = bse_apply_device(h, psi, hpsi, n_vec);
+      cudaEventRecord(e1, st);
+      if (s == BSE_OK) s = bse_cuda_check(h, cudaEventSynchronize(e1), "autotune timing");
+      if (s != BSE_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_split = sp;
+        best_stages = sg;
+      }
+    }
+    if (s != BSE_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(psi);
+  cudaFree(hpsi);
+  if (s == BSE_OK) s = bse_tc_status(h);
+  if (s != BSE_OK) {
+    ts->smax = keep_split;
+    ts->stages = keep_stages;
+    return s;
+  }
+  ts->smax = best_split;
+  ts->stages = best_stages;
+  if (split_out) *split_out = best_split;
+  if (stages_out) *stages_out = best_stages;
+  return BSE_OK;
 }
 
 bse_status bse_tc_status(bse_handle* h) {

@@ -85,6 +85,22 @@ def test_cubic_k_meshes_match_oracle(n, prec):
             assert rel(out[v], ref[v]) < TOL[prec], (nx, v)
 
 
+def test_autotune_choice_keeps_parity():
+    """bse_autotune picks a split-K factor and a pipeline depth from its
+    candidate sets by timing; H psi with the chosen tiles still matches the
+    oracle, and the FP64 form has nothing to tune."""
+    s = S.tiny_system(49, n_alpha=6, nk=(4, 4, 4), n_bands=40, nx=(8, 8, 8), n_proj=3)
+    sysg = bse.System(s, precision="split_bf16", max_vec=2)
+    sp, sg = sysg.autotune(n_vec=2, reps=2)
+    assert sp in (1, 2, 4, 8) and sg in (3, 4, 6, 8)
+    psi = S.complex_normal(np.random.default_rng(49), (2, s.dim))
+    out = sysg.apply_h(psi)
+    ref = O.apply_h(s, psi)
+    for v in range(2):
+        assert rel(out[v], ref[v]) < TOL["split_bf16"]
+    assert bse.System(s, precision="fp64").autotune() == (0, 0)
+
+
 @pytest.mark.parametrize("max_vec", [3, 2])
 def test_haydock_batched_vectors_split_bf16(max_vec):
     """Three start vectors (polarisations) in one Haydock call: fused epilogue

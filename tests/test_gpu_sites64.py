@@ -3,7 +3,8 @@ n^3, n = 4..8; grid m^3, m = 12..20; 32..256 bands; 1 or 6 core states), 96.6
 GB of complex64-equivalent u_nk drawn on the GPU, run in the split-bf16 form as
 one graph-captured launch of 200 Haydock steps per site (bse_haydock_batch).
 
-* every site completes its 200 steps;
+* every site completes its 200 steps, with the tiles chosen by rule and again
+  after a per-site timed tile search (bse_autotune);
 * the batched coefficients of sampled sites equal a single-site run of the
   same handle bit for bit (same kernels, fixed-order reductions);
 * for sampled sites covering every mesh size 4..8 and both edge types, the
@@ -56,7 +57,16 @@ def test_64_uneven_sites_one_launch():
     t0 = time.perf_counter()
     outs, sts = bse.haydock_batch(systems, bs, STEPS)
     el = time.perf_counter() - t0
-    print("64 sites x %d steps: %.2f s, %.2f spectra/s" % (STEPS, el, N_SITES / el))
+    print("64 sites x %d steps, tiles by rule: %.2f s, %.2f spectra/s" % (STEPS, el, N_SITES / el))
+    assert np.all(sts == bse.BSE_OK)
+    # per-site timed tile search, then the same batch again
+    tiles = [g.autotune(n_vec=1, reps=3) for g in systems]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs, sts = bse.haydock_batch(systems, bs, STEPS)
+    el = time.perf_counter() - t0
+    print("64 sites x %d steps, tuned tiles: %.2f s, %.2f spectra/s; (split, stages) %s"
+          % (STEPS, el, N_SITES / el, sorted(set(tiles))))
     assert np.all(sts == bse.BSE_OK)
     for a, bc, st in outs:
         assert st[0] == STEPS
