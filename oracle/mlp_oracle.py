@@ -249,6 +249,75 @@ def spai_grad(params, x, diag, z, rs, apply_h, quantize=True, scaled=False):
     return tot, _outputs_grad(q16, cache, o, p, g_p, g_u, g_v)
 
 
+def apply_adjoint(p, u, v, x):
+    """P^H x = conj(p) x + V (U^H x) / N."""
+    n = x.shape[0]
+    return np.conj(p) * x + v @ (u.conj().T @ x) / n
+
+
+def _krylov_residual(p, u, v, z, r, apply_h, k):
+    """y_0 = r, y_i = (H - z) P y_{i-1}; c = argmin |r - sum_i c_i y_i| over the
+    k vectors y_1..y_k (least squares, numpy.linalg.lstsq); returns (ys, c, res)."""
+    ys = [r]
+    for _ in range(k):
+        t = apply(p, u, v, ys[-1])
+        ys.append(apply_h(t) - z * t)
+    kmat = np.stack(ys[1:], 1)
+    c = np.linalg.lstsq(kmat, r, rcond=None)[0]
+    return ys, c, r - kmat @ c
+
+
+def krylov_loss(params, x, diag, z, rs, apply_h, k, quantize=True):
+    """k-step minimal-residual loss on probes r_t:
+    sum_t min_{deg q <= k, q(0) = 1} |q((H - z) P) r_t|^2 / |r_t|^2,
+    the squared residual reduction of k steps of right-preconditioned GMRES
+    started from residual r_t (k = 1: the scaled approximate-inverse loss)."""
+    o, _ = forward(fp16(params) if quantize else params, x)
+    p, u, v = assemble(o, diag, z)
+    tot = 0.0
+    for r in rs:
+        _, _, res = _krylov_residual(p, u, v, z, r, apply_h, k)
+        tot += float(np.vdot(res, res).real / np.vdot(r, r).real)
+    return tot
+
+
+def krylov_grad(params, x, diag, z, rs, apply_h, k, quantize=True):
+    """(loss, gradient) of krylov_loss.  The least-squares coefficients c are
+    stationary, so d|res|^2 = -2 Re <res, sum_i c_i dy_i>, and with
+    dy_i = sum_{m<i} ((H - z)P)^m (H - z) dP y_{i-1-m}:
+      dL_t = -w_t Re sum_{m + j <= k-1} c_{m+j+1} <q_m, dP y_j>,
+    q_m = (H - z)^H s_m, s_0 = res, s_{m+1} = P^H q_m, w_t = 2/|r_t|^2.
+    Summing over m first, G_j = -sum_m conj(c_{m+j+1}) q_m pairs with y_j
+    exactly as g_t pairs with r_t in spai_grad."""
+    q16 = fp16(params) if quantize else params
+    o, cache = forward(q16, x)
+    p, u, v = assemble(o, diag, z)
+    n = x.shape[0]
+    g_p = np.zeros(n, dtype=np.complex128)
+    g_u = np.zeros((n, RANK), dtype=np.complex128)
+    g_v = np.zeros((n, RANK), dtype=np.complex128)
+    tot = 0.0
+    for r in rs:
+        ys, c, res = _krylov_residual(p, u, v, z, r, apply_h, k)
+        w = 2.0 / np.vdot(r, r).real
+        tot += 0.5 * w * np.vdot(res, res).real
+        qs = []
+        s = res
+        for _ in range(k):
+            q = apply_h(s) - np.conj(z) * s
+            qs.append(q)
+            s = apply_adjoint(p, u, v, q)
+        for j in range(k):
+            g = np.zeros(n, dtype=np.complex128)
+            for m in range(k - j):
+                g -= np.conj(c[m + j]) * qs[m]
+            y = ys[j]
+            g_p += w * g * np.conj(y)
+            g_u += w * np.outer(g, np.conj(v.conj().T @ y / n))
+            g_v += w * np.outer(y, np.conj(u.conj().T @ g)) / n
+    return tot, _outputs_grad(q16, cache, o, p, g_p, g_u, g_v)
+
+
 def adam(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam step (t counts from 1); returns new (params, m, v)."""
     newp, newm, newv = {}, {}, {}

@@ -76,6 +76,50 @@ def test_spai_gradient_matches_central_differences(problem, scaled):
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, idx, fd, an)
 
 
+@pytest.mark.parametrize("k", [1, 4])
+def test_krylov_gradient_matches_central_differences(problem, k):
+    """k-step minimal-residual loss: back-propagation through the forward and
+    adjoint Krylov chains (2k applications of H per probe) against central
+    differences of the FP64 network."""
+    s, diag, z, x, rs, es, params = problem
+    p16 = M.fp16(params)
+    happly = lambda v: O.apply_h(s, v)
+    tot, g = M.krylov_grad(p16, x, diag, z, rs, happly, k)
+    assert tot == pytest.approx(M.krylov_loss(p16, x, diag, z, rs, happly, k), rel=1e-12)
+    rng = np.random.default_rng(10 + k)
+    h = 1e-6
+    for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        flat = p16[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=3, replace=False):
+            up = {kk: v.copy() for kk, v in p16.items()}
+            dn = {kk: v.copy() for kk, v in p16.items()}
+            up[name].reshape(-1)[idx] += h
+            dn[name].reshape(-1)[idx] -= h
+            fd = (M.krylov_loss(up, x, diag, z, rs, happly, k, quantize=False)
+                  - M.krylov_loss(dn, x, diag, z, rs, happly, k, quantize=False)) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, idx, fd, an)
+
+
+def test_krylov_loss_is_gmres_residual(problem):
+    """The k-step loss on one probe equals the squared relative residual of k
+    steps of right-preconditioned GMRES from x_0 = 0 for the right-hand side r
+    (oracle GMRES, no restart), and one step equals the scaled approximate-
+    inverse loss."""
+    s, diag, z, x, rs, es, params = problem
+    o, _ = M.forward(M.fp16(params), x)
+    p, u, v = M.assemble(o, diag, z)
+    happly = lambda vv: O.apply_h(s, vv)
+    r = rs[0]
+    k = 3
+    a = lambda vv: happly(vv) - z * vv
+    xg, it, rel = O.gmres(happly, r, z, lambda vv: M.apply(p, u, v, vv), rtol=1e-300, restart=k, max_iter=k)
+    resid = np.linalg.norm(r - a(xg)) / np.linalg.norm(r)
+    assert M.krylov_loss(params, x, diag, z, [r], happly, k) == pytest.approx(resid ** 2, rel=1e-8)
+    assert M.krylov_loss(params, x, diag, z, rs, happly, 1) == pytest.approx(
+        M.spai_loss(params, x, diag, z, rs, happly, scaled=True), rel=1e-10)
+
+
 def test_spai_optimal_diagonal_closed_form():
     """For a diagonal P the approximate-inverse loss over all unit probes is
     |A diag(p) - I|_F^2, minimised column by column by
