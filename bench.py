@@ -380,7 +380,7 @@ def main():
         gm["jacobi"] = leg(sys_g, "jacobi", zs, xg)
         # learned preconditioner: the network's prior (last layer zero: the damped
         # diagonal) and the network after training on the GPU at shifts between the
-        # measured ones (residual probes of plain GMRES(30), minimal-residual loss)
+        # measured ones (residual probes of plain GMRES(30), 10-step minimal-residual loss)
         net = bse.MLP(S.mlp_init(0))
         bse.attach_mlp(sys_g, net)
         gm["mlp_prior"] = leg(sys_g, "mlp", zs, xg)
@@ -389,7 +389,7 @@ def main():
             zt = np.linspace(-5.0 + 0.5 * step, 30.0 - 0.5 * step, args.train_omega) + 0.5j
             torch.cuda.synchronize()
             t_tr = time.perf_counter()
-            hist = net.train([sys_g], [b], zt, epochs=args.train_epochs, batch=1, lr=1e-3, seed=1, scaled=True)
+            hist = net.train([sys_g], [b], zt, epochs=args.train_epochs, batch=1, lr=1e-3, seed=1, steps=10)
             torch.cuda.synchronize()
             t_tr = time.perf_counter() - t_tr
             gm["mlp_trained"] = leg(sys_g, "mlp", zs, xg)

@@ -192,13 +192,14 @@ bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_
  *   U_jq = o_{2+q} + i o_{10+q},  V_jq = o_{18+q} + i o_{26+q}  (q < 8),
  * and GMRES uses the right preconditioner P = diag(p) + U V^H / N.  Parameters
  * are packed w1[12][128], b1[128], w2[128][128], b2[128], w3[128][34], b3[34]
- * (bse_mlp_n_params() floats, FP32 master copy).  Training minimises the
- * approximate-inverse loss on residual probes r_t
- *   sum_t |alpha_t (H - z) P r_t - r_t|^2 / |r_t|^2,
- * with alpha_t = 1 (plain) or alpha_t = <(H-z)P r_t, r_t> / |(H-z)P r_t|^2
- * (scaled: each term is then the residual reduction of one minimal-residual
- * step with the preconditioned operator), with Adam (beta 0.9/0.999, eps
- * 1e-8).  Supports n_alpha <= 6. */
+ * (bse_mlp_n_params() floats, FP32 master copy).  Training minimises, over
+ * residual probes r_t, the k-step minimal-residual loss
+ *   sum_t min_{deg q <= k, q(0) = 1} |q((H - z) P) r_t|^2 / |r_t|^2,
+ * the squared residual reduction of k steps of right-preconditioned GMRES
+ * started from residual r_t (its gradient runs a forward and an adjoint
+ * Krylov chain: 2k applications of H per probe); k = 0 selects the plain
+ * approximate-inverse loss sum_t |(H - z) P r_t - r_t|^2 / |r_t|^2.  Adam
+ * (beta 0.9/0.999, eps 1e-8).  Supports n_alpha <= 6. */
 typedef struct bse_mlp bse_mlp;
 
 long long bse_mlp_n_params(void);
@@ -210,12 +211,12 @@ bse_status bse_mlp_params(const bse_mlp* m, float* out);
 /* Network outputs o [N][34] (FP32) for the handle's system at one shift. */
 bse_status bse_mlp_outputs(bse_handle* h, bse_mlp* m, double omega, double gamma, float* out);
 /* Loss and its gradient with respect to the parameters (grad [n_params],
- * host or device, overwritten) for one shift and n_probes <= 64 probes
- * r [n_probes][N] (device memory); scaled selects the minimal-residual form.
- * Costs two applications of H per probe (the handle's precision, in chunks
- * of its max_vec). */
+ * host or device, overwritten) for one shift and n_probes probes
+ * r [n_probes][N] (device memory); krylov_steps k in 0..16 with
+ * n_probes * max(k, 1) <= 64.  Costs 2 max(k, 1) applications of H per probe
+ * (the handle's precision, in chunks of its max_vec). */
 bse_status bse_mlp_loss_grad(bse_handle* h, bse_mlp* m, double omega, double gamma, int n_probes,
-                             const bse_c128* r, int scaled, double* loss, float* grad);
+                             const bse_c128* r, int krylov_steps, double* loss, float* grad);
 /* One Adam step with the given gradient (host or device). */
 bse_status bse_mlp_adam_step(bse_mlp* m, const float* grad, double lr);
 /* Harvest residual probes on each system (handles hs, start vectors bs [N]
@@ -225,7 +226,7 @@ bse_status bse_mlp_adam_step(bse_mlp* m, const float* grad, double lr);
  * n_sys*n_z samples in a seeded shuffled order with one Adam step per `batch`
  * samples.  loss_per_epoch [epochs] (host) receives the mean sample loss. */
 bse_status bse_mlp_train(bse_handle* const* hs, const bse_c128* const* bs, int n_sys, const bse_c128* z,
-                         int n_z, int epochs, int batch, double lr, int seed, int scaled, bse_mlp* m,
+                         int n_z, int epochs, int batch, double lr, int seed, int krylov_steps, bse_mlp* m,
                          double* loss_per_epoch);
 /* Attach (or detach with NULL) the network used by BSE_PRECOND_MLP; the caller
  * keeps ownership and must keep it alive while GMRES runs. */

@@ -310,19 +310,20 @@ class MLP:
         sysg._check(lib().bse_mlp_outputs(sysg.h, self.h, float(omega), float(gamma), out.ctypes.data))
         return out
 
-    def loss_grad(self, sysg, omega, gamma, r, scaled=True):
-        """(loss, grad [n]) of the approximate-inverse loss on the device probe array r [T][N]."""
+    def loss_grad(self, sysg, omega, gamma, r, steps=10):
+        """(loss, grad [n]) on the device probe array r [T][N]: the k-step
+        minimal-residual loss (steps = k >= 1) or the plain approximate-inverse loss (steps = 0)."""
         g = np.empty(self.n, dtype=np.float32)
         loss = ctypes.c_double()
         sysg._check(lib().bse_mlp_loss_grad(sysg.h, self.h, float(omega), float(gamma), r.shape[0], _ptr(r),
-                                            int(bool(scaled)), ctypes.byref(loss), g.ctypes.data))
+                                            int(steps), ctypes.byref(loss), g.ctypes.data))
         return loss.value, g
 
     def adam_step(self, grad, lr):
         g = np.ascontiguousarray(grad, dtype=np.float32)
         _chk(lib().bse_mlp_adam_step(self.h, g.ctypes.data, float(lr)))
 
-    def train(self, systems, bs, z, epochs, batch, lr, seed=0, scaled=True):
+    def train(self, systems, bs, z, epochs, batch, lr, seed=0, steps=10):
         """Harvest residual probes on each System and train; returns the mean loss per epoch."""
         n = len(systems)
         hs = (ctypes.c_void_p * n)(*[s.h.value for s in systems])
@@ -331,7 +332,7 @@ class MLP:
         zz = np.ascontiguousarray(np.atleast_1d(z), dtype=np.complex128)
         hist = np.zeros(epochs)
         st = lib().bse_mlp_train(hs, bp, n, zz.ctypes.data, zz.size, int(epochs), int(batch), float(lr), int(seed),
-                                 int(bool(scaled)), self.h, hist.ctypes.data)
+                                 int(steps), self.h, hist.ctypes.data)
         if st != BSE_OK:
             raise BSEError(st, lib().bse_last_error(systems[0].h).decode())
         return hist

@@ -8,9 +8,12 @@
 // and the right preconditioner P = diag(p) + U V^H / N of GMRES for
 // (H - z) x = b (the resolvent of Eq. 2).  Weights are stored in FP16 and every
 // product accumulates in FP32; the FP32 master copy, Adam moments and
-// gradients live next to them.  Training minimises sum_t |P r_t - e_t|^2/|e_t|^2
-// over residual/error pairs harvested from unpreconditioned GMRES histories.
-// Every reduction is a fixed-order two-stage sum.
+// gradients live next to them.  Training minimises, over residual probes r_t
+// harvested from unpreconditioned GMRES histories, the k-step minimal-residual
+// loss sum_t min_{deg q <= k, q(0)=1} |q((H - z)P) r_t|^2/|r_t|^2 (the residual
+// reduction of k steps of preconditioned GMRES; k = 0 selects the plain
+// approximate-inverse loss |(H - z)P r_t - r_t|^2/|r_t|^2).  Every reduction
+// is a fixed-order two-stage sum.
 #include "bse_internal.cuh"
 
 #include <cuda_fp16.h>
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(256) pc_red_c(const float2* __restrict__ v, co
 
 // out[t][q] = sum_blk part[blk][t][q]
 __global__ void pc_red_finish(const double2* __restrict__ part, int nblk, int T, double2* __restrict__ out) {
-  const int e = threadIdx.x;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= T * (RANK + 1)) return;
   double a = 0, b = 0;
   for (int blk = 0; blk < nblk; ++blk) {
@@ -321,20 +324,28 @@ __global__ void __launch_bounds__(256) pc_red_spai(const float2* __restrict__ u,
   }
 }
 
-// dO per row from the probe statistics (C: V^H r and |r|^2, L: U^H g and |q|^2),
-// delta := g_t = (H - conj(z)) q_t, w_t = 2/|r_t|^2
+// dO per row from T (vector r_t, adjoint g_t) pairs and their statistics (C:
+// V^H r and |r|^2, L: U^H g): g_p = sum_t w_t g_t conj(r_t), g_U = sum_t w_t
+// g_t c_t^H, g_V = sum_t w_t r_t lambda_t^H / N.  Weights: wts[t] when given,
+// else w_t = 2/|r_t|^2 (0 for |r_t|^2 <= r2_min).
 __global__ void pc_dout(const float2* __restrict__ p, const float2* __restrict__ u, const double2* __restrict__ C,
                         const double2* __restrict__ L, const double2* __restrict__ r, const double2* __restrict__ G,
-                        int T, int N, double r2_min, float* __restrict__ dO) {
+                        int T, int N, double r2_min, const double* __restrict__ wts, float* __restrict__ dO) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
   const float2 pp = p[j];
   float gpx = 0.f, gpy = 0.f;
   float gux[RANK] = {0}, guy[RANK] = {0}, gvx[RANK] = {0}, gvy[RANK] = {0};
   for (int t = 0; t < T; ++t) {
-    const double r2 = C[t * (RANK + 1) + RANK].x;
-    if (!(r2 > r2_min)) continue;   // residuals of an already converged solve carry no information
-    const float w = (float)(2.0 / r2);
+    float w;
+    if (wts) {
+      w = (float)wts[t];
+      if (w == 0.f) continue;
+    } else {
+      const double r2 = C[t * (RANK + 1) + RANK].x;
+      if (!(r2 > r2_min)) continue;   // residuals of an already converged solve carry no information
+      w = (float)(2.0 / r2);
+    }
     float2 c[RANK];
 #pragma unroll
     for (int q = 0; q < RANK; ++q) {
@@ -496,6 +507,7 @@ struct bse_mlp {
   float* wpart = nullptr; // WG_BLOCKS * 129 * 128
   double2* red = nullptr; // reduction scratch
   double2* stats = nullptr;
+  size_t red_cap = 0, stats_cap = 0;   // entries
   double2* probe = nullptr;   // P r, (H - z) P r - r, (H - conj z)(...) for the probes
   size_t probe_cap = 0;
 };
@@ -606,77 +618,106 @@ __global__ void spai_q(double2* __restrict__ Q, const double2* __restrict__ Y, c
   }
 }
 
-// partials of (sum_j conj(ay_tj) r_tj, sum_j |ay_tj|^2) per probe t, block-major [blk][t]
-__global__ void __launch_bounds__(256) spai_mr_red(const double2* __restrict__ AY, const double2* __restrict__ R,
-                                                   int N, double2* __restrict__ part) {
-  const int t = blockIdx.y;
-  double sr = 0, si = 0, yy = 0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-    const double2 a = AY[(size_t)t * N + j], r = R[(size_t)t * N + j];
-    sr += a.x * r.x + a.y * r.y;
-    si += a.x * r.y - a.y * r.x;
-    yy += a.x * a.x + a.y * a.y;
-  }
-  __shared__ double s0[8], s1[8], s2[8];
-  for (int off = 16; off > 0; off >>= 1) {
-    sr += __shfl_xor_sync(0xffffffffu, sr, off);
-    si += __shfl_xor_sync(0xffffffffu, si, off);
-    yy += __shfl_xor_sync(0xffffffffu, yy, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s0[threadIdx.x >> 5] = sr;
-    s1[threadIdx.x >> 5] = si;
-    s2[threadIdx.x >> 5] = yy;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int w = 0; w < 8; ++w) {
-      a += s0[w];
-      b += s1[w];
-      c += s2[w];
-    }
-    part[((size_t)blockIdx.x * gridDim.y + t) * 2] = make_double2(a, b);
-    part[((size_t)blockIdx.x * gridDim.y + t) * 2 + 1] = make_double2(c, 0.0);
-  }
-}
-
-// alpha_t = <ay_t, r_t> / |ay_t|^2: the minimal-residual step along (H - z) P r_t
-__global__ void spai_mr_alpha(const double2* __restrict__ part, int nblk, int T, double2* __restrict__ alpha) {
-  const int t = threadIdx.x;
-  if (t >= T) return;
-  double a = 0, b = 0, c = 0;
-  for (int blk = 0; blk < nblk; ++blk) {
-    const double2 s = part[((size_t)blk * T + t) * 2], y = part[((size_t)blk * T + t) * 2 + 1];
-    a += s.x;
-    b += s.y;
-    c += y.x;
-  }
-  alpha[t] = c > 0 ? make_double2(a / c, b / c) : make_double2(0.0, 0.0);
-}
-
-// q = alpha_t ay - r  (ay is in Q on entry)
-__global__ void spai_mr_q(double2* __restrict__ Q, const double2* __restrict__ R, const double2* __restrict__ alpha,
-                          int N, size_t n) {
-  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
-    const double2 al = alpha[j / N], a = Q[j], r = R[j];
-    Q[j] = make_double2(al.x * a.x - al.y * a.y - r.x, al.x * a.y + al.y * a.x - r.y);
-  }
-}
-
-// g = conj(alpha_t) (HQ - conj(z) q), alpha_t = 1 when alpha is null  (HQ is in G on entry)
-__global__ void spai_g(double2* __restrict__ G, const double2* __restrict__ Q, const double2* __restrict__ alpha,
-                       double zr, double zi, int N, size_t n) {
+// g = HQ - conj(z) q  (HQ is in G on entry)
+__global__ void spai_g(double2* __restrict__ G, const double2* __restrict__ Q, double zr, double zi, size_t n) {
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
     const double2 hq = G[j], q = Q[j];
-    const double gx = hq.x - (zr * q.x + zi * q.y), gy = hq.y - (zr * q.y - zi * q.x);
-    if (alpha) {
-      const double2 al = alpha[j / N];
-      G[j] = make_double2(al.x * gx + al.y * gy, al.x * gy - al.y * gx);
-    } else {
-      G[j] = make_double2(gx, gy);
+    G[j] = make_double2(hq.x - (zr * q.x + zi * q.y), hq.y - (zr * q.y - zi * q.x));
+  }
+}
+
+// ---- k-step minimal-residual loss ----
+constexpr int KMAX = 16;   // largest number of Krylov steps of the loss
+
+// partials of <Y_i, Y_j> (i = 0..j) per probe t for one j: part[blk][t][i][j], Y [(k+1)][T][N]
+template <int NI>
+__global__ void __launch_bounds__(256) ks_dots(const double2* __restrict__ Y, int T, int N, int j, int k,
+                                               double2* __restrict__ part) {
+  const int t = blockIdx.y;
+  double ar[NI], ai[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) ar[i] = ai[i] = 0.0;
+  const size_t tn = (size_t)T * N;
+  const double2* yj = Y + (size_t)j * tn + (size_t)t * N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+    const double2 b = yj[e];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      if (i <= j) {
+        const double2 a = Y[(size_t)i * tn + (size_t)t * N + e];
+        ar[i] += a.x * b.x + a.y * b.y;   // conj(a) b
+        ai[i] += a.x * b.y - a.y * b.x;
+      }
     }
   }
+  __shared__ double sr[8][NI], si[8][NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    for (int off = 16; off > 0; off >>= 1) {
+      ar[i] += __shfl_xor_sync(0xffffffffu, ar[i], off);
+      ai[i] += __shfl_xor_sync(0xffffffffu, ai[i], off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sr[threadIdx.x >> 5][i] = ar[i];
+      si[threadIdx.x >> 5][i] = ai[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x <= j && threadIdx.x < NI) {
+    double a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) {
+      a += sr[w][threadIdx.x];
+      b += si[w][threadIdx.x];
+    }
+    part[(((size_t)blockIdx.x * T + t) * (k + 1) + threadIdx.x) * (k + 1) + j] = make_double2(a, b);
+  }
+}
+
+// gram[t][i][j] = sum_blk part[blk][t][i][j] for i <= j (fixed order)
+__global__ void ks_dots_finish(const double2* __restrict__ part, int nblk, int T, int k, double2* __restrict__ gram) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = (k + 1) * (k + 1);
+  if (e >= T * per) return;
+  const int i = (e % per) / (k + 1), j = e % (k + 1);
+  if (i > j) return;
+  double a = 0, b = 0;
+  for (int blk = 0; blk < nblk; ++blk) {
+    const double2 v = part[(size_t)blk * T * per + e];
+    a += v.x;
+    b += v.y;
+  }
+  gram[e] = make_double2(a, b);
+}
+
+// out_t = (x0 ? x0_t : 0) + sum_{i < n} coef[t][i] X_i,t   (X_i,t = X + i*xs + t*N; coef [T][KMAX])
+__global__ void ks_lincomb(double2* __restrict__ out, const double2* __restrict__ x0, const double2* __restrict__ X,
+                           size_t xs, int n, const double2* __restrict__ coef, int T, int N) {
+  const int t = blockIdx.y;
+  __shared__ double2 cf[KMAX];
+  if (threadIdx.x < KMAX) cf[threadIdx.x] = coef[t * KMAX + threadIdx.x];
+  __syncthreads();
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+    double2 acc = x0 ? x0[(size_t)t * N + e] : make_double2(0.0, 0.0);
+    for (int i = 0; i < n; ++i) {
+      const double2 c = cf[i], v = X[(size_t)i * xs + (size_t)t * N + e];
+      acc.x += c.x * v.x - c.y * v.y;
+      acc.y += c.x * v.y + c.y * v.x;
+    }
+    out[(size_t)t * N + e] = acc;
+  }
+}
+
+// Y = HT - z T (HT in Y on entry); conj != 0: Y = HT - conj(z) T
+__global__ void ks_shift(double2* __restrict__ Y, const double2* __restrict__ Tv, double zr, double zi, size_t n) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
+    const double2 hy = Y[j], y = Tv[j];
+    Y[j] = make_double2(hy.x - (zr * y.x - zi * y.y), hy.y - (zr * y.y + zi * y.x));
+  }
+}
+
+__global__ void conj_f2(const float2* __restrict__ a, float2* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2(a[i].x, -a[i].y);
 }
 
 bse_status apply_h_chunks(bse_handle* h, const double2* in, double2* out, int n) {
@@ -688,52 +729,10 @@ bse_status apply_h_chunks(bse_handle* h, const double2* in, double2* out, int n)
   return BSE_OK;
 }
 
-// Loss sum_t |alpha_t (H - z) P r_t - r_t|^2 / |r_t|^2 over the T residual
-// probes r [T][N] (device), alpha_t = 1 or (scaled) the minimal-residual step
-// <(H - z) P r_t, r_t> / |(H - z) P r_t|^2, and its gradient accumulated into m->g.
-bse_status loss_grad(bse_handle* h, bse_mlp* m, double omega, double gamma, int T, const double2* r, float2* p,
-                     float2* u, float2* v, double* loss_out, double r2_min, bool scaled) {
-  Act a;
-  bse_status s = forward(h, m, omega, gamma, &a);
-  if (s != BSE_OK) return s;
-  const int N = (int)h->N;
+// backward through the three layers from dO (per-row output gradients), into m->g
+bse_status backward(bse_handle* h, bse_mlp* m, const Act& a) {
   cudaStream_t st = h->stream;
-  const size_t tn = (size_t)T * N;
-  if (m->probe_cap < 3 * tn) {
-    if (m->probe) cudaFree(m->probe);
-    m->probe = nullptr;
-    m->probe_cap = 0;
-    if (!dmalloc(&m->probe, 3 * tn * sizeof(double2))) return bse_fail(h, BSE_ERR_OOM, "probe buffers");
-    m->probe_cap = 3 * tn;
-  }
-  double2 *Y = m->probe, *Q = Y + tn, *G = Q + tn;
-  BSE_PROF(h, BSE_K_PREP, pc_assemble<<<(N + 255) / 256, 256, 0, st>>>(a.O, h->jdiag, omega, gamma, N, p, u, v));
-  double2* part = m->red;
-  double2* alpha = scaled ? m->stats + 2 * T * (RANK + 1) : nullptr;
-  // Y = P r, Q = alpha (H - z) Y - r, G = conj(alpha) (H - conj z) Q: two applications of H per probe
-  s = bse_mlp_apply(h, p, u, v, r, N, T, nullptr, Y, N, 0, part, 0);
-  if (s == BSE_OK) s = apply_h_chunks(h, Y, Q, T);
-  if (s != BSE_OK) return s;
-  const int ge = (int)std::min<size_t>((tn + 255) / 256, 4096);
-  if (scaled) {
-    BSE_PROF(h, BSE_K_PREP, spai_q<<<ge, 256, 0, st>>>(Q, Y, nullptr, omega, gamma, tn));
-    BSE_PROF(h, BSE_K_PREP, spai_mr_red<<<dim3(NRED, T), 256, 0, st>>>(Q, r, N, part));
-    BSE_PROF(h, BSE_K_PREP, spai_mr_alpha<<<1, 64, 0, st>>>(part, NRED, T, alpha));
-    BSE_PROF(h, BSE_K_PREP, spai_mr_q<<<ge, 256, 0, st>>>(Q, r, alpha, N, tn));
-  } else {
-    BSE_PROF(h, BSE_K_PREP, spai_q<<<ge, 256, 0, st>>>(Q, Y, r, omega, gamma, tn));
-  }
-  s = apply_h_chunks(h, Q, G, T);
-  if (s != BSE_OK) return s;
-  BSE_PROF(h, BSE_K_PREP, spai_g<<<ge, 256, 0, st>>>(G, Q, alpha, omega, gamma, N, tn));
-  double2* C = m->stats;
-  double2* L = m->stats + T * (RANK + 1);
-  BSE_PROF(h, BSE_K_PREP, pc_red_c<<<dim3(NRED, T), 256, 0, st>>>(v, r, r, N, part));
-  BSE_PROF(h, BSE_K_PREP, pc_red_finish<<<1, 256, 0, st>>>(part, NRED, T, C));
-  BSE_PROF(h, BSE_K_PREP, pc_red_spai<<<dim3(NRED, T), 256, 0, st>>>(u, G, Q, N, part));
-  BSE_PROF(h, BSE_K_PREP, pc_red_finish<<<1, 256, 0, st>>>(part, NRED, T, L));
-  BSE_PROF(h, BSE_K_PREP, pc_dout<<<(N + 255) / 256, 256, 0, st>>>(p, u, C, L, r, G, T, N, r2_min, a.dO));
-  // backward through the three layers
+  const int N = (int)h->N;
   const int g = (N + RB - 1) / RB;
   BSE_PROF(h, BSE_K_PREP, mlp_wgrad<<<WG_BLOCKS, 256, 0, st>>>(a.H2, WID, a.dO, F_OUT, N, m->wpart));
   BSE_PROF(h, BSE_K_PREP,
@@ -751,6 +750,61 @@ bse_status loss_grad(bse_handle* h, bse_mlp* m, double omega, double gamma, int 
   BSE_PROF(h, BSE_K_PREP,
            mlp_wgrad_reduce<<<((F_IN + 1) * WID + 255) / 256, 256, 0, st>>>(m->wpart, WG_BLOCKS, F_IN, WID, m->g,
                                                                              OFF_W1, OFF_B1));
+  return bse_cuda_check(h, cudaGetLastError(), "mlp backward");
+}
+
+bse_status ensure_probe(bse_handle* h, bse_mlp* m, size_t n) {
+  if (m->probe_cap >= n) return BSE_OK;
+  if (m->probe) cudaFree(m->probe);
+  m->probe = nullptr;
+  m->probe_cap = 0;
+  if (!dmalloc(&m->probe, n * sizeof(double2))) return bse_fail(h, BSE_ERR_OOM, "probe buffers");
+  m->probe_cap = n;
+  return BSE_OK;
+}
+
+bool grow(double2** buf, size_t* cap, size_t n) {
+  if (*cap >= n) return true;
+  double2* b = nullptr;
+  if (!dmalloc(&b, n * sizeof(double2))) return false;
+  cudaFree(*buf);
+  *buf = b;
+  *cap = n;
+  return true;
+}
+
+// Plain approximate-inverse loss sum_t |(H - z) P r_t - r_t|^2 / |r_t|^2 over
+// the T probes r [T][N] (device); gradient accumulated into m->g.
+bse_status loss_grad_spai(bse_handle* h, bse_mlp* m, double omega, double gamma, int T, const double2* r, float2* p,
+                          float2* u, float2* v, double* loss_out, double r2_min) {
+  Act a;
+  bse_status s = forward(h, m, omega, gamma, &a);
+  if (s != BSE_OK) return s;
+  const int N = (int)h->N;
+  cudaStream_t st = h->stream;
+  const size_t tn = (size_t)T * N;
+  if ((s = ensure_probe(h, m, 3 * tn)) != BSE_OK) return s;
+  double2 *Y = m->probe, *Q = Y + tn, *G = Q + tn;
+  BSE_PROF(h, BSE_K_PREP, pc_assemble<<<(N + 255) / 256, 256, 0, st>>>(a.O, h->jdiag, omega, gamma, N, p, u, v));
+  double2* part = m->red;
+  // Y = P r, Q = (H - z) Y - r, G = (H - conj z) Q: two applications of H per probe
+  s = bse_mlp_apply(h, p, u, v, r, N, T, nullptr, Y, N, 0, part, 0);
+  if (s == BSE_OK) s = apply_h_chunks(h, Y, Q, T);
+  if (s != BSE_OK) return s;
+  const int ge = (int)std::min<size_t>((tn + 255) / 256, 4096);
+  BSE_PROF(h, BSE_K_PREP, spai_q<<<ge, 256, 0, st>>>(Q, Y, r, omega, gamma, tn));
+  s = apply_h_chunks(h, Q, G, T);
+  if (s != BSE_OK) return s;
+  BSE_PROF(h, BSE_K_PREP, spai_g<<<ge, 256, 0, st>>>(G, Q, omega, gamma, tn));
+  double2* C = m->stats;
+  double2* L = m->stats + T * (RANK + 1);
+  BSE_PROF(h, BSE_K_PREP, pc_red_c<<<dim3(NRED, T), 256, 0, st>>>(v, r, r, N, part));
+  BSE_PROF(h, BSE_K_PREP, pc_red_finish<<<1, 256, 0, st>>>(part, NRED, T, C));
+  BSE_PROF(h, BSE_K_PREP, pc_red_spai<<<dim3(NRED, T), 256, 0, st>>>(u, G, Q, N, part));
+  BSE_PROF(h, BSE_K_PREP, pc_red_finish<<<1, 256, 0, st>>>(part, NRED, T, L));
+  BSE_PROF(h, BSE_K_PREP,
+           pc_dout<<<(N + 255) / 256, 256, 0, st>>>(p, u, C, L, r, G, T, N, r2_min, nullptr, a.dO));
+  if ((s = backward(h, m, a)) != BSE_OK) return s;
   if (loss_out) {
     std::vector<double2> hs(2 * T * (RANK + 1));
     bse_status cs = bse_cuda_check(
@@ -766,6 +820,203 @@ bse_status loss_grad(bse_handle* h, bse_mlp* m, double omega, double gamma, int 
     *loss_out = tot;
   }
   return bse_cuda_check(h, cudaGetLastError(), "mlp loss/grad");
+}
+
+// Solve the k x k Hermitian system G c = hv (row-major G, FP64) by Cholesky on
+// the diagonally scaled matrix; a vanishing pivot adds a small ridge and retries.
+bool solve_gram(std::vector<double2> G, std::vector<double2> hv, int k, std::vector<double2>& c) {
+  std::vector<double> sc(k);
+  for (int i = 0; i < k; ++i) sc[i] = G[i * k + i].x > 0 ? 1.0 / sqrt(G[i * k + i].x) : 1.0;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      G[i * k + j].x *= sc[i] * sc[j];
+      G[i * k + j].y *= sc[i] * sc[j];
+    }
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const double ridge = attempt ? pow(10.0, -14 + 3 * attempt) : 0.0;
+    std::vector<double2> Lm(G);
+    for (int i = 0; i < k; ++i) Lm[i * k + i].x += ridge;
+    bool ok = true;
+    for (int j = 0; j < k && ok; ++j) {   // L L^H, lower triangle
+      double d = Lm[j * k + j].x;
+      for (int q = 0; q < j; ++q) d -= Lm[j * k + q].x * Lm[j * k + q].x + Lm[j * k + q].y * Lm[j * k + q].y;
+      if (!(d > 1e-300)) {
+        ok = false;
+        break;
+      }
+      const double ljj = sqrt(d);
+      Lm[j * k + j] = make_double2(ljj, 0.0);
+      for (int i = j + 1; i < k; ++i) {
+        double2 s = Lm[i * k + j];   // G_ij (scaled); G Hermitian: use the lower entry G[i][j]
+        for (int q = 0; q < j; ++q) {
+          const double2 a = Lm[i * k + q], b = Lm[j * k + q];   // s -= a conj(b)
+          s.x -= a.x * b.x + a.y * b.y;
+          s.y -= a.y * b.x - a.x * b.y;
+        }
+        Lm[i * k + j] = make_double2(s.x / ljj, s.y / ljj);
+      }
+    }
+    if (!ok) continue;
+    std::vector<double2> y(k);
+    for (int i = 0; i < k; ++i) {   // L y = sc * hv
+      double2 s = make_double2(hv[i].x * sc[i], hv[i].y * sc[i]);
+      for (int q = 0; q < i; ++q) {
+        const double2 a = Lm[i * k + q], b = y[q];
+        s.x -= a.x * b.x - a.y * b.y;
+        s.y -= a.x * b.y + a.y * b.x;
+      }
+      y[i] = make_double2(s.x / Lm[i * k + i].x, s.y / Lm[i * k + i].x);
+    }
+    c.assign(k, make_double2(0.0, 0.0));
+    for (int i = k - 1; i >= 0; --i) {   // L^H x = y
+      double2 s = y[i];
+      for (int q = i + 1; q < k; ++q) {
+        const double2 a = Lm[q * k + i], b = c[q];   // conj(L[q][i]) x_q
+        s.x -= a.x * b.x + a.y * b.y;
+        s.y -= a.x * b.y - a.y * b.x;
+      }
+      c[i] = make_double2(s.x / Lm[i * k + i].x, s.y / Lm[i * k + i].x);
+    }
+    for (int i = 0; i < k; ++i) c[i] = make_double2(c[i].x * sc[i], c[i].y * sc[i]);
+    return true;
+  }
+  return false;
+}
+
+// k-step minimal-residual loss sum_t min_{deg q <= k, q(0)=1} |q((H - z)P) r_t|^2/|r_t|^2
+// over the T probes r [T][N] (device) and its gradient into m->g.
+//   forward chain  Y_0 = r, Y_i = (H - z) P Y_{i-1} (k applications of H);
+//   least squares  c = argmin |r - sum_i c_i Y_i| from the FP64 Gram matrix;
+//   adjoint chain  s_0 = r - sum c_i Y_i, Q_m = (H - conj z) s_m, s_{m+1} = P^H Q_m;
+//   pairs          (Y_j, G_j), G_j = -sum_m conj(c_{m+j+1}) Q_m, weight 2/|r_t|^2.
+bse_status loss_grad_krylov(bse_handle* h, bse_mlp* m, double omega, double gamma, int T, const double2* r,
+                            float2* p, float2* u, float2* v, double* loss_out, double r2_min, int k) {
+  Act a;
+  bse_status s = forward(h, m, omega, gamma, &a);
+  if (s != BSE_OK) return s;
+  const int N = (int)h->N;
+  cudaStream_t st = h->stream;
+  const size_t tn = (size_t)T * N;
+  // Y [k+1][T][N], Q [k][T][N], GJ [k][T][N], Tt [T][N]
+  if ((s = ensure_probe(h, m, (size_t)(3 * k + 2) * tn)) != BSE_OK) return s;
+  double2* Y = m->probe;
+  double2* Q = Y + (size_t)(k + 1) * tn;
+  double2* GJ = Q + (size_t)k * tn;
+  double2* Tt = GJ + (size_t)k * tn;
+  const int per = (k + 1) * (k + 1);
+  const int TT = k * T;
+  cudaStreamSynchronize(st);   // the scratch below may be reallocated
+  if (!grow(&m->red, &m->red_cap, std::max((size_t)NRED * T * per, (size_t)NRED * TT * (RANK + 1))) ||
+      !grow(&m->stats, &m->stats_cap, (size_t)T * per + (size_t)T * KMAX + TT + 2 * (size_t)TT * (RANK + 1)))
+    return bse_fail(h, BSE_ERR_OOM, "k-step loss scratch");
+  double2* part = m->red;
+  float2* pc = (float2*)a.dA;   // conj(p): the first N float2 of a scratch activation, free until backward
+  BSE_PROF(h, BSE_K_PREP, pc_assemble<<<(N + 255) / 256, 256, 0, st>>>(a.O, h->jdiag, omega, gamma, N, p, u, v));
+  BSE_PROF(h, BSE_K_PREP, conj_f2<<<(N + 255) / 256, 256, 0, st>>>(p, pc, N));
+  const int ge = (int)std::min<size_t>((tn + 255) / 256, 4096);
+  cudaMemcpyAsync(Y, r, tn * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+  for (int i = 1; i <= k; ++i) {
+    s = bse_mlp_apply(h, p, u, v, Y + (size_t)(i - 1) * tn, N, T, nullptr, Tt, N, 0, part, 0);
+    if (s == BSE_OK) s = apply_h_chunks(h, Tt, Y + (size_t)i * tn, T);
+    if (s != BSE_OK) return s;
+    BSE_PROF(h, BSE_K_PREP, ks_shift<<<ge, 256, 0, st>>>(Y + (size_t)i * tn, Tt, omega, gamma, tn));
+  }
+  // Gram matrix <Y_i, Y_j>, 0 <= i <= j <= k
+  for (int j = 0; j <= k; ++j)
+    BSE_PROF(h, BSE_K_PREP, ks_dots<KMAX + 1><<<dim3(NRED, T), 256, 0, st>>>(Y, T, N, j, k, part));
+  double2* gram = m->stats;   // [T][k+1][k+1]
+  BSE_PROF(h, BSE_K_PREP, ks_dots_finish<<<(T * per + 255) / 256, 256, 0, st>>>(part, NRED, T, k, gram));
+  std::vector<double2> hg((size_t)T * per);
+  s = bse_cuda_check(h, cudaMemcpyAsync(hg.data(), gram, hg.size() * sizeof(double2), cudaMemcpyDeviceToHost, st),
+                     "gram");
+  if (s == BSE_OK) s = bse_cuda_check(h, cudaStreamSynchronize(st), "gram sync");
+  if (s != BSE_OK) return s;
+  // host: least-squares coefficients, loss, pair weights and adjoint coefficients
+  std::vector<double2> cres((size_t)T * KMAX, make_double2(0.0, 0.0));
+  std::vector<double> wts((size_t)k * T, 0.0);
+  std::vector<std::vector<double2>> cs(T);
+  double tot = 0.0;
+  for (int t = 0; t < T; ++t) {
+    const double2* gt = hg.data() + (size_t)t * per;
+    auto at = [&](int i, int j) {   // <Y_i, Y_j> for any i, j (Hermitian completion)
+      if (i <= j) return gt[i * (k + 1) + j];
+      const double2 q = gt[j * (k + 1) + i];
+      return make_double2(q.x, -q.y);
+    };
+    const double r2 = at(0, 0).x;
+    cs[t].assign(k, make_double2(0.0, 0.0));
+    if (!(r2 > r2_min)) continue;   // probe of an already converged solve
+    std::vector<double2> G((size_t)k * k), hv(k);
+    for (int i = 0; i < k; ++i) {
+      for (int j = 0; j < k; ++j) G[i * k + j] = at(i + 1, j + 1);
+      hv[i] = at(i + 1, 0);   // <Y_i, r>
+    }
+    if (!solve_gram(G, hv, k, cs[t])) continue;
+    // |res|^2 = |r|^2 - Re(c^H h) at the least-squares optimum
+    double ch = 0.0;
+    for (int i = 0; i < k; ++i) ch += cs[t][i].x * hv[i].x + cs[t][i].y * hv[i].y;
+    tot += std::max(0.0, r2 - ch) / r2;
+    for (int j = 0; j < k; ++j) wts[(size_t)j * T + t] = 2.0 / r2;
+    for (int i = 0; i < k; ++i) cres[(size_t)t * KMAX + i] = make_double2(-cs[t][i].x, -cs[t][i].y);
+  }
+  if (loss_out) *loss_out = tot;
+  double2* dcoef = m->stats + (size_t)T * per;   // [T][KMAX] coefficient staging
+  double* dwts = (double*)(dcoef + (size_t)T * KMAX);
+  s = bse_cuda_check(h, cudaMemcpyAsync(dcoef, cres.data(), cres.size() * sizeof(double2), cudaMemcpyHostToDevice, st),
+                     "coefficients");
+  if (s != BSE_OK) return s;
+  // residual s_0 = r - sum_i c_i Y_i (into Tt), adjoint chain into Q
+  const dim3 gl((unsigned)std::min((N + 255) / 256, 512), (unsigned)T);
+  BSE_PROF(h, BSE_K_PREP, ks_lincomb<<<gl, 256, 0, st>>>(Tt, Y, Y + tn, tn, k, dcoef, T, N));
+  for (int mm = 0; mm < k; ++mm) {
+    s = apply_h_chunks(h, Tt, Q + (size_t)mm * tn, T);
+    if (s != BSE_OK) return s;
+    BSE_PROF(h, BSE_K_PREP, ks_shift<<<ge, 256, 0, st>>>(Q + (size_t)mm * tn, Tt, omega, -gamma, tn));
+    if (mm + 1 < k) {   // s_{m+1} = P^H Q_m = conj(p) Q_m + V (U^H Q_m) / N
+      s = bse_mlp_apply(h, pc, v, u, Q + (size_t)mm * tn, N, T, nullptr, Tt, N, 0, part, 0);
+      if (s != BSE_OK) return s;
+    }
+  }
+  // G_j = -sum_{m <= k-1-j} conj(c_{m+j+1}) Q_m
+  for (int j = 0; j < k; ++j) {
+    std::vector<double2> cj((size_t)T * KMAX, make_double2(0.0, 0.0));
+    for (int t = 0; t < T; ++t)
+      for (int mm = 0; mm + j < k; ++mm) {
+        const double2 c = cs[t][mm + j];
+        cj[(size_t)t * KMAX + mm] = make_double2(-c.x, c.y);
+      }
+    s = bse_cuda_check(h, cudaMemcpyAsync(dcoef, cj.data(), cj.size() * sizeof(double2), cudaMemcpyHostToDevice, st),
+                       "adjoint coefficients");
+    if (s != BSE_OK) return s;
+    BSE_PROF(h, BSE_K_PREP,
+             ks_lincomb<<<gl, 256, 0, st>>>(GJ + (size_t)j * tn, nullptr, Q, tn, k - j, dcoef, T, N));
+    // the next iteration overwrites dcoef: wait for this combination
+    s = bse_cuda_check(h, cudaStreamSynchronize(st), "adjoint sync");
+    if (s != BSE_OK) return s;
+  }
+  // k*T pairs (Y_j, G_j) with their statistics, then dO and the backward pass
+  s = bse_cuda_check(h, cudaMemcpyAsync(dwts, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+                     "pair weights");
+  if (s != BSE_OK) return s;
+  double2* C = m->stats + (size_t)T * per + (size_t)T * KMAX + TT;   // after the weights (TT doubles)
+  double2* L = C + (size_t)TT * (RANK + 1);
+  BSE_PROF(h, BSE_K_PREP, pc_red_c<<<dim3(NRED, TT), 256, 0, st>>>(v, Y, Y, N, part));
+  BSE_PROF(h, BSE_K_PREP, pc_red_finish<<<(TT * (RANK + 1) + 255) / 256, 256, 0, st>>>(part, NRED, TT, C));
+  BSE_PROF(h, BSE_K_PREP, pc_red_spai<<<dim3(NRED, TT), 256, 0, st>>>(u, GJ, GJ, N, part));
+  BSE_PROF(h, BSE_K_PREP, pc_red_finish<<<(TT * (RANK + 1) + 255) / 256, 256, 0, st>>>(part, NRED, TT, L));
+  BSE_PROF(h, BSE_K_PREP,
+           pc_dout<<<(N + 255) / 256, 256, 0, st>>>(p, u, C, L, Y, GJ, TT, N, 0.0, dwts, a.dO));
+  if ((s = backward(h, m, a)) != BSE_OK) return s;
+  s = bse_cuda_check(h, cudaStreamSynchronize(st), "loss/grad sync");
+  if (s != BSE_OK) return s;
+  return bse_cuda_check(h, cudaGetLastError(), "mlp k-step loss/grad");
+}
+
+// krylov_steps = 0: plain approximate-inverse loss; >= 1: k-step minimal-residual loss
+bse_status loss_grad(bse_handle* h, bse_mlp* m, double omega, double gamma, int T, const double2* r, float2* p,
+                     float2* u, float2* v, double* loss_out, double r2_min, int krylov_steps) {
+  if (krylov_steps <= 0) return loss_grad_spai(h, m, omega, gamma, T, r, p, u, v, loss_out, r2_min);
+  return loss_grad_krylov(h, m, omega, gamma, T, r, p, u, v, loss_out, r2_min, krylov_steps);
 }
 
 }  // namespace
@@ -820,6 +1071,8 @@ bse_status bse_mlp_create(bse_mlp** out, const float* params, long long n_params
     mlp_free(m);
     return BSE_ERR_OOM;
   }
+  m->red_cap = (size_t)NRED * 64 * (RANK + 1);
+  m->stats_cap = (size_t)3 * 64 * (RANK + 1);
   if (cudaMemcpy(m->w, params, nb, cudaMemcpyDefault) != cudaSuccess) {
     cudaGetLastError();
     mlp_free(m);
@@ -864,8 +1117,9 @@ bse_status bse_mlp_outputs(bse_handle* h, bse_mlp* m, double omega, double gamma
 }
 
 bse_status bse_mlp_loss_grad(bse_handle* h, bse_mlp* m, double omega, double gamma, int n_probes, const bse_c128* r,
-                             int scaled, double* loss, float* grad) {
-  if (!h || !m || !r || !loss || !grad || n_probes < 1 || n_probes > 64)
+                             int krylov_steps, double* loss, float* grad) {
+  if (!h || !m || !r || !loss || !grad || n_probes < 1 || n_probes > 64 || krylov_steps < 0 ||
+      krylov_steps > KMAX || n_probes * std::max(krylov_steps, 1) > 64)
     return h ? bse_fail(h, BSE_ERR_INVALID_ARG, "mlp_loss_grad: bad arguments") : BSE_ERR_INVALID_ARG;
   if (!bse_is_device_ptr(r)) return bse_fail(h, BSE_ERR_INVALID_ARG, "mlp_loss_grad: r must be device memory");
   const int n_pairs = n_probes;
@@ -878,7 +1132,7 @@ bse_status bse_mlp_loss_grad(bse_handle* h, bse_mlp* m, double omega, double gam
     return bse_fail(h, BSE_ERR_OOM, "mlp_loss_grad scratch");
   }
   cudaMemsetAsync(m->g, 0, (size_t)NPARAM * sizeof(float), h->stream);
-  bse_status s = loss_grad(h, m, omega, gamma, n_pairs, (const double2*)r, p, u, v, loss, 0.0, scaled != 0);
+  bse_status s = loss_grad(h, m, omega, gamma, n_pairs, (const double2*)r, p, u, v, loss, 0.0, krylov_steps);
   if (s == BSE_OK)
     s = bse_cuda_check(h, cudaMemcpyAsync(grad, m->g, (size_t)NPARAM * sizeof(float), cudaMemcpyDefault, h->stream),
                        "grad copy");
@@ -933,8 +1187,9 @@ __global__ void __launch_bounds__(256) sq_norm_rows(const double2* __restrict__ 
 
 extern "C" bse_status bse_mlp_train(bse_handle* const* hs, const bse_c128* const* bs, int n_sys,
                                     const bse_c128* z, int n_z, int epochs, int batch, double lr, int seed,
-                                    int scaled, bse_mlp* m, double* loss_per_epoch) {
-  if (!hs || !bs || !z || !m || n_sys < 1 || n_z < 1 || epochs < 1 || batch < 1 || !(lr > 0))
+                                    int krylov_steps, bse_mlp* m, double* loss_per_epoch) {
+  if (!hs || !bs || !z || !m || n_sys < 1 || n_z < 1 || epochs < 1 || batch < 1 || !(lr > 0) ||
+      krylov_steps < 0 || krylov_steps > KMAX)
     return BSE_ERR_INVALID_ARG;
   // residual probes r_t of unpreconditioned GMRES(30) after 0 (r = b), 1, 2 and 4 restart cycles
   const int cycles[4] = {0, 1, 2, 4};
@@ -1027,7 +1282,7 @@ extern "C" bse_status bse_mlp_train(bse_handle* const* hs, const bse_c128* const
       double l = 0;
       // probes with |r| <= 1e-5 |b| belong to an already converged solve and are skipped
       st = loss_grad(h, m, zh[zi].x, zh[zi].y, T, R[samples[k].sys] + (size_t)zi * T * N, p, u, v, &l,
-                     1e-10 * b2[samples[k].sys], scaled != 0);
+                     1e-10 * b2[samples[k].sys], krylov_steps);
       tot += l;
       if (++inb == batch || k + 1 == samples.size()) {
         m->t += 1;

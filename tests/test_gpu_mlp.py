@@ -47,10 +47,11 @@ def test_outputs_match_oracle(tiny):
         assert rel(out, ref) < 2e-4
 
 
-@pytest.mark.parametrize("scaled", [False, True])
-def test_gradient_matches_oracle(tiny, scaled):
-    """Approximate-inverse loss on three probes (two FP64 applications of H
-    per probe on the GPU) and its gradient against the oracle's."""
+@pytest.mark.parametrize("steps", [0, 1, 4])
+def test_gradient_matches_oracle(tiny, steps):
+    """Loss on three probes and its gradient against the oracle's: the plain
+    approximate-inverse loss (steps = 0) and the k-step minimal-residual loss
+    (forward and adjoint Krylov chains through FP64 applications of H)."""
     torch = pytest.importorskip("torch")
     s, flat = tiny
     sysg = bse.System(s, precision="fp64", max_vec=2)
@@ -58,10 +59,15 @@ def test_gradient_matches_oracle(tiny, scaled):
     rng = np.random.default_rng(12)
     rs = S.complex_normal(rng, (3, s.dim))
     om, g = 4.0, 0.5
-    loss, grad = net.loss_grad(sysg, om, g, torch.from_numpy(rs).cuda(), scaled=scaled)
+    loss, grad = net.loss_grad(sysg, om, g, torch.from_numpy(rs).cuda(), steps=steps)
     diag = O.jacobi_diag(s).reshape(-1)
-    lo, go = M.spai_grad(M.unpack(flat.astype(np.float64)), M.system_features(s, diag, om, g), diag, om + 1j * g,
-                         list(rs), lambda v: O.apply_h(s, v), scaled=scaled)
+    params = M.unpack(flat.astype(np.float64))
+    feats = M.system_features(s, diag, om, g)
+    happly = lambda v: O.apply_h(s, v)
+    if steps == 0:
+        lo, go = M.spai_grad(params, feats, diag, om + 1j * g, list(rs), happly)
+    else:
+        lo, go = M.krylov_grad(params, feats, diag, om + 1j * g, list(rs), happly, steps)
     assert loss == pytest.approx(lo, rel=1e-4)
     gg = M.unpack(grad.astype(np.float64))
     for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
@@ -99,32 +105,37 @@ def trained(reduced):
     s, b = reduced
     sysg = bse.System(s, precision="fp64", max_vec=4)
     net = bse.MLP(S.mlp_init(0))
-    hist = net.train([sysg], [b], TRAIN_Z, epochs=10, batch=1, lr=1e-3, seed=1, scaled=True)
+    hist = net.train([sysg], [b], TRAIN_Z, epochs=10, batch=1, lr=1e-3, seed=1, steps=10)
     return net, hist
 
 
 def test_training_reduces_loss(trained):
-    """The mean sample loss (minimal-residual form) falls over the epochs."""
+    """The mean sample loss (10-step minimal-residual form) falls over the epochs."""
     net, hist = trained
     assert np.all(np.isfinite(hist))
     assert hist[-1] < 0.95 * hist[0]
 
 
-def test_trained_network_beats_no_preconditioner(reduced, trained):
+def test_trained_network_beats_prior_and_no_preconditioner(reduced, trained):
     """Gain of the trained network at shifts it was not trained on: GMRES(30)
     reaches the same solution (true residual 1e-8) in fewer iterations than
-    GMRES without a preconditioner."""
+    with the untrained network (the damped diagonal it starts from) and than
+    without a preconditioner."""
     s, b = reduced
     net, _ = trained
     sysg = bse.System(s, precision="fp64", max_vec=3)
-    bse.attach_mlp(sysg, net)
     x0, it0, r0, st0 = sysg.gmres(b, HELD_OUT_Z, rtol=1e-8, restart=30, max_iter=3000, precond="none")
+    prior = bse.MLP(S.mlp_init(0))
+    bse.attach_mlp(sysg, prior)
+    xp, itp, rp, stp = sysg.gmres(b, HELD_OUT_Z, rtol=1e-8, restart=30, max_iter=3000, precond="mlp")
+    bse.attach_mlp(sysg, net)
     x1, it1, r1, st1 = sysg.gmres(b, HELD_OUT_Z, rtol=1e-8, restart=30, max_iter=3000, precond="mlp")
-    assert st0 == bse.BSE_OK and st1 == bse.BSE_OK
+    assert st0 == bse.BSE_OK and stp == bse.BSE_OK and st1 == bse.BSE_OK
     for j in range(len(HELD_OUT_Z)):
         assert rel(x1[j], x0[j]) < 1e-6
     assert np.all(r1 <= 1e-8)
     assert np.all(it1 < it0), (it0, it1)
+    assert np.all(it1 < itp), (itp, it1)
 
 
 def test_gmres_with_prior_network(reduced):
