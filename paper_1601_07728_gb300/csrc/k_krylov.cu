@@ -302,6 +302,44 @@ bse_status cgs2(bse_handle* h, const double2* basis, long long bstride, double2*
   return BSE_OK;
 }
 
+// DGKS test after one classical Gram-Schmidt pass: with s_after = |w|^2 (from
+// partial sums) and s_proj = sum_j |h_j|^2 of the coefficients just removed,
+// |w_before|^2 = s_after + s_proj, and a second pass is needed where more than
+// half of |w|^2 was removed (|w_after| < |w_before| / sqrt 2, i.e. s_after < s_proj).
+__global__ void __launch_bounds__(RB) gs_dgks_mask(const double2* __restrict__ partial, int nblk,
+                                                   const double2* __restrict__ coef, int coef_stride, int nj,
+                                                   const int* __restrict__ mask, int* __restrict__ mask2) {
+  const int v = blockIdx.x;
+  const double2 s = sum_partials(partial, v, nblk);
+  if (threadIdx.x == 0) {
+    double proj = 0.0;
+    for (int j = 0; j < nj; ++j) {
+      const double2 c = coef[(size_t)v * coef_stride + j];
+      proj += c.x * c.x + c.y * c.y;
+    }
+    const int on = mask ? mask[v] : 1;
+    mask2[v] = on && !(s.x >= proj);   // NaN also takes the second pass
+  }
+}
+
+// Classical Gram-Schmidt with the DGKS criterion: one pass, and a second only
+// for the systems whose first pass cancelled more than half of |w|^2.
+bse_status cgs_dgks(bse_handle* h, const double2* basis, long long bstride, double2* w, int nv, int nj,
+                    double2* partial, double2* coef, int coef_stride, double2* hacc, int hacc_stride,
+                    const int* mask, int* mask2) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(NBLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, NBLK, coef, coef_stride, hacc, hacc_stride));
+  BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask));
+  BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, nv), RB, 0, st>>>(w, N, nullptr, 0, N, partial));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dgks_mask<<<nv, RB, 0, st>>>(partial, NBLK, coef, coef_stride, nj, mask, mask2));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(NBLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask2));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, NBLK, coef, coef_stride, hacc, hacc_stride));
+  BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask2));
+  return BSE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // continued fraction  (Eqs. 1-2)
 // ---------------------------------------------------------------------------
@@ -1029,6 +1067,8 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
   TRY(dalloc(h, &active, (size_t)n_z * sizeof(int), "active")); fr.add(active);
   TRY(dalloc(h, &jdone, (size_t)n_z * sizeof(int), "jdone")); fr.add(jdone);
   TRY(dalloc(h, &mask, (size_t)n_z * sizeof(int), "mask")); fr.add(mask);
+  int* mask2;
+  TRY(dalloc(h, &mask2, (size_t)n_z * sizeof(int), "reorthogonalisation mask")); fr.add(mask2);
   double2* Wc;
   int* didx;
   TRY(dalloc(h, &Wc, (size_t)n_z * N * sizeof(double2), "gmres packed H T")); fr.add(Wc);
@@ -1082,8 +1122,9 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
       }
       TRY(apply_chunked(h, T, Wc, ns));
       BSE_PROF(h, BSE_K_RECURSION, gm_scatter_shift<<<ec, 256, 0, st>>>(Wc, T, z, W, N, didx));
-      TRY(cgs2(h, V, vstride, W, n_z, j + 1, partial, coef, m + 1, Hs + (size_t)j * (m + 1),
-               (m + 1) * m, mask));
+      // Arnoldi: classical Gram-Schmidt, repeated where the DGKS test asks for it
+      TRY(cgs_dgks(h, V, vstride, W, n_z, j + 1, partial, coef, m + 1, Hs + (size_t)j * (m + 1),
+                   (m + 1) * m, mask, mask2));
       BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_z), RB, 0, st>>>(W, N, nullptr, 0, N, partial));
       BSE_PROF(h, BSE_K_RECURSION, gm_givens<<<n_z, RB, 0, st>>>(partial, NBLK, Hs, cs, sn, g, hnorm, m, j, bnorm, rtol, max_iter,
                                    active, iters_d, jdone, est));

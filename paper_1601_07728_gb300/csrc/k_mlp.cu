@@ -414,17 +414,26 @@ __global__ void __launch_bounds__(256) pc_apply_red(const double2* __restrict__ 
   const int s = blockIdx.y, sys = idx ? idx[s] : s;
   const double2* xs = x + (size_t)(idx ? sys : s) * xstride;
   const float2* vs = V + (size_t)sys * fstride * N * RANK;
-  double cr[RANK], ci[RANK];
+  // FP32 products and per-thread sums (V is FP32; FP64 here would make this
+  // pass FP64-bound), FP64 across the block and the grid
+  float fr[RANK], fi[RANK];
 #pragma unroll
-  for (int q = 0; q < RANK; ++q) cr[q] = ci[q] = 0.0;
+  for (int q = 0; q < RANK; ++q) fr[q] = fi[q] = 0.f;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
-    const double2 xx = xs[j];
+    const double2 xd = xs[j];
+    const float2 xx = make_float2((float)xd.x, (float)xd.y);
 #pragma unroll
     for (int q = 0; q < RANK; ++q) {
       const float2 vv = vs[j * RANK + q];
-      cr[q] += vv.x * xx.x + vv.y * xx.y;
-      ci[q] += vv.x * xx.y - vv.y * xx.x;
+      fr[q] += vv.x * xx.x + vv.y * xx.y;
+      fi[q] += vv.x * xx.y - vv.y * xx.x;
     }
+  }
+  double cr[RANK], ci[RANK];
+#pragma unroll
+  for (int q = 0; q < RANK; ++q) {
+    cr[q] = fr[q];
+    ci[q] = fi[q];
   }
   __shared__ double sr[8][RANK], si[8][RANK];
 #pragma unroll
