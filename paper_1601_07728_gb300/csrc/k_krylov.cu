@@ -246,6 +246,7 @@ bse_status apply_chunked(bse_handle* h, const double2* in, double2* out, int n_v
 // Gram-Schmidt projections <basis_j|w> for JB basis vectors at a time: w is
 // read once per group of JB (not once per basis vector).  partial[v][j][blk].
 constexpr int GS_JB = 8;
+constexpr int GS_BLK = 64;   // blocks per vector of the multi-dot: long loops, few partials to reduce
 __global__ void __launch_bounds__(RB) gs_dot_multi(const double2* __restrict__ basis, long long bstride,
                                                    const double2* __restrict__ w, long long N, int nj,
                                                    double2* __restrict__ partial, const int* __restrict__ mask) {
@@ -295,8 +296,8 @@ bse_status cgs2(bse_handle* h, const double2* basis, long long bstride, double2*
   cudaStream_t st = h->stream;
   const long long N = h->N;
   for (int pass = 0; pass < 2; ++pass) {
-    BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(NBLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask));
-    BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, NBLK, coef, coef_stride, hacc, hacc_stride));
+    BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(GS_BLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask));
+    BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, GS_BLK, coef, coef_stride, hacc, hacc_stride));
     BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask));
   }
   return BSE_OK;
@@ -329,13 +330,13 @@ bse_status cgs_dgks(bse_handle* h, const double2* basis, long long bstride, doub
                     const int* mask, int* mask2) {
   cudaStream_t st = h->stream;
   const long long N = h->N;
-  BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(NBLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask));
-  BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, NBLK, coef, coef_stride, hacc, hacc_stride));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(GS_BLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, GS_BLK, coef, coef_stride, hacc, hacc_stride));
   BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask));
   BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, nv), RB, 0, st>>>(w, N, nullptr, 0, N, partial));
   BSE_PROF(h, BSE_K_RECURSION, gs_dgks_mask<<<nv, RB, 0, st>>>(partial, NBLK, coef, coef_stride, nj, mask, mask2));
-  BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(NBLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask2));
-  BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, NBLK, coef, coef_stride, hacc, hacc_stride));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(GS_BLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask2));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, GS_BLK, coef, coef_stride, hacc, hacc_stride));
   BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask2));
   return BSE_OK;
 }
