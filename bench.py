@@ -39,7 +39,7 @@ WORKLOAD_DESC = ("L2,3 edge with multiplets: 6 core states (SO split 5.7 eV), k-
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default=os.environ.get("BSE_BENCH_PRECISION", "split_bf16"))
