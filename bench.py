@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tiles", default="auto",
+                   help="tensor-core tiles of the headline run: auto (timed search) or SPLIT_K,STAGES")
     p.add_argument("--polarisations", type=int, default=3,
                    help="start vectors of the batched-polarisation Haydock measurement (<= 1: skip)")
     p.add_argument("--gmres-omega", type=int, default=40, help="shifts in the GMRES measurement (0 = skip)")
@@ -227,7 +229,13 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     sysg = bse.System(s, precision=args.precision, max_vec=1, stream=stream.cuda_stream)
-    tiles = sysg.autotune(n_vec=1, reps=5)   # timed tile search (split-K, pipeline stages), before any timing
+    if args.tiles == "auto":
+        tiles = sysg.autotune(n_vec=1, reps=5)   # timed tile search (split-K, pipeline stages), before any timing
+        tiles_by = "bse_autotune timed search"
+    else:
+        tiles = tuple(int(v) for v in args.tiles.split(","))
+        sysg.set_tiles(*tiles)
+        tiles_by = "fixed (--tiles)"
     n = sysg.dim
     db = torch.from_numpy(b).to("cuda")
     K, W = args.steps, args.warmup
@@ -466,7 +474,7 @@ def main():
                        "recursion": "f64 Haydock, no re-orthogonalisation", "n_vec": 1, "dim": n,
                        "l2": "inputs larger than L2 (u_nk 1.07 GB), no flush", "parallelism": "replicas",
                        "tiles": {"grid_to_band_split_k": tiles[0], "pipeline_stages": tiles[1],
-                                 "chosen_by": "bse_autotune timed search"}},
+                                 "chosen_by": tiles_by}},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                          "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3, "launches": nl},

@@ -295,6 +295,12 @@ typedef enum {
  * buffer when needed) and synchronises the handle's stream, so call it
  * outside any stream capture, e.g. right after bse_setup. */
 bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* split_out, int* stages_out);
+/* Sets the tensor-core tile parameters directly (e.g. to reproduce a measured
+ * configuration): split_k in 1..16 (0: the rule of bse_setup), stages 2..8
+ * (0: the rule; more than fit shared memory are capped).  Other precisions:
+ * no-op.  Synchronises the handle's stream; may reallocate the partial-sum
+ * buffer. */
+bse_status bse_set_tiles(bse_handle* h, int split_k, int stages);
 
 /* Measurement aid, no counterpart in the paper: when enabled, every kernel
  * launch of the handle is bracketed by CUDA events on the handle's stream

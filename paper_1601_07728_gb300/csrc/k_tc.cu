@@ -988,6 +988,40 @@ int bse_tc_final_blocks(const bse_handle* h) {
   return (int)bk;
 }
 
+// Fixed tile parameters (see bse_set_tiles in bse.h).
+extern "C" bse_status bse_set_tiles(bse_handle* h, int split_k, int stages) {
+  if (!h) return BSE_ERR_INVALID_ARG;
+  if (split_k < 0 || split_k > 16 || stages < 0 || stages == 1 || stages > 8)
+    return bse_fail(h, BSE_ERR_INVALID_ARG, "set_tiles: need 0 <= split_k <= 16 and stages 0 or 2..8");
+  if (h->prec != BSE_PREC_SPLIT_BF16 || !h->tmap_host) return BSE_OK;
+  TcState* ts = (TcState*)h->tmap_host;
+  {
+    const bse_status ss = bse_cuda_check(h, cudaStreamSynchronize(h->stream), "set_tiles sync");
+    if (ss != BSE_OK) return ss;
+  }
+  if (split_k == 0) {   // back to the rule of bse_setup
+    const int kbt = (h->nx + TC_KB - 1) / TC_KB;
+    const int units = h->nk * ((2 * h->nb + TC_M - 1) / TC_M);
+    int sp = 1;
+    while (units * sp < 8 * ts->sms && kbt / (sp * 2) >= 8) sp *= 2;
+    split_k = sp;
+  }
+  if (split_k > ts->part_cap) {
+    float2* np = nullptr;
+    if (cudaMalloc((void**)&np, (size_t)split_k * h->nk * h->nb * h->na * h->max_vec * sizeof(float2)) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return bse_fail(h, BSE_ERR_OOM, "set_tiles: partial-sum buffer");
+    }
+    cudaFree(h->part);
+    h->part = (float*)np;
+    ts->part_cap = split_k;
+  }
+  ts->smax = split_k;
+  ts->stages = stages;
+  return BSE_OK;
+}
+
 // Timed search over the tensor-core tile parameters of one handle (see
 // bse_autotune in bse.h).
 extern "C" bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* split_out, int* stages_out) {

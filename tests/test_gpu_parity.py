@@ -94,10 +94,13 @@ def test_autotune_choice_keeps_parity():
     sp, sg = sysg.autotune(n_vec=2, reps=2)
     assert sp in (1, 2, 4, 8) and sg in (3, 4, 6, 8)
     psi = S.complex_normal(np.random.default_rng(49), (2, s.dim))
-    out = sysg.apply_h(psi)
     ref = O.apply_h(s, psi)
-    for v in range(2):
-        assert rel(out[v], ref[v]) < TOL["split_bf16"]
+    for tiles in (None, (1, 3), (16, 8), (0, 0)):
+        if tiles is not None:
+            sysg.set_tiles(*tiles)   # fixed choices, including more stages than fit (capped) and the rule
+        out = sysg.apply_h(psi)
+        for v in range(2):
+            assert rel(out[v], ref[v]) < TOL["split_bf16"], tiles
     assert bse.System(s, precision="fp64").autotune() == (0, 0)
 
 
