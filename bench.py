@@ -69,6 +69,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The slowest rank's value of a per-rank time (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, seconds_max, world):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -290,13 +305,9 @@ def main():
     prof = sysg.profile_read()
     sysg.profile(False)
     sysg.haydock(db, K, a=a_d, bcoef=b_d, steps=st_d)   # restore the K-step result for steps_done
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist)
     steps_done = int(st_d.item())
-    value = world * steps_done / (t_max / 1e3)
+    value = job_rate(steps_done, t_max / 1e3, world)
 
     # spectrum error of this run against the FP64 oracle's stored Haydock
     # coefficients for the same workload and start vector (both spectra
@@ -335,13 +346,9 @@ def main():
         sys3.haydock(b3, K, a=a3, bcoef=bb3, steps=st3)
         p1.record(stream)
         torch.cuda.synchronize()
-        pms = p0.elapsed_time(p1)
-        if dist is not None:
-            t = torch.tensor([pms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            pms = float(t.item())
+        pms = max_over_ranks(p0.elapsed_time(p1), dist)
         done3 = int(st3.sum().item())
-        pol = {"n_vec": npol, "matvecs_per_s": world * done3 / (pms / 1e3), "ms_per_step": pms / K,
+        pol = {"n_vec": npol, "matvecs_per_s": job_rate(done3, pms / 1e3, world), "ms_per_step": pms / K,
                "note": "polarisations batched as GEMM columns; u_nk read once per step for all of them"}
         if spec is not None:
             kk = spec["steps"]
@@ -369,13 +376,9 @@ def main():
             _, g_it, g_rr, g_st = system.gmres(db, z, rtol=1e-6, restart=30, max_iter=args.gmres_max_iter,
                                                precond=pc, x=x)
             torch.cuda.synchronize()
-            g_el = time.perf_counter() - g0
-            if dist is not None:
-                t = torch.tensor([g_el], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                g_el = float(t.item())
+            g_el = max_over_ranks(time.perf_counter() - g0, dist)
             conv = int(np.sum(g_rr <= 1e-6))
-            return {"solves_per_s": world * conv / g_el, "seconds": g_el, "converged": conv, "n_omega": len(z),
+            return {"solves_per_s": job_rate(conv, g_el, world), "seconds": g_el, "converged": conv, "n_omega": len(z),
                     "iters_mean": float(np.mean(g_it)), "iters_max": int(np.max(g_it)),
                     "max_rel_resid": float(np.max(g_rr)), "gpu_launches": system.launches - l1}
 
@@ -435,12 +438,8 @@ def main():
     for _ in range(k_e2e):
         sysg.apply_h(hpn, hon)
     torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    e2e = world * k_e2e / el
+    el = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e = job_rate(k_e2e, el, world)
 
     # roofline of the dominant kernel class
     peak, peak_kind = peaks()
