@@ -241,11 +241,9 @@ bse_status bse_jacobi_diag(bse_handle* h, double* diag);
 /* Short-range (local direct + exchange) term alone, out = (A (x) I)^H M (A (x) I) psi,
  * computed without allocating any memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need
- * the term -- code that runs while its stream is being captured into a CUDA
- * graph (allocation is not a stream-ordered operation and is refused there),
- * plug-ins whose host framework owns every device byte through its own pool,
- * and real-time loops that cannot afford the synchronisation an allocation
- * implies.  No handle is used and nothing is allocated, by this library or by
+ * the term -- plug-ins whose host framework owns every device byte through
+ * its own pool, and real-time loops that cannot afford the synchronisation an
+ * allocation implies.  No handle is used and nothing is allocated, by this library or by
  * any library it calls.
  *   a_proj [n_proj][n_kb], m_sr [n_alpha*n_proj]^2 (index (alpha, p), alpha
  *   slow), psi and out [n_vec][n_alpha][n_kb], all complex128 DEVICE memory

@@ -1,9 +1,7 @@
 // Short-range term of H with no allocation at all: the split-K scratch of the
 // projection lives in a fixed file-scope device array instead of memory that
 // a handle would cudaMalloc.  For callers that cannot allocate device memory
-// at the point where they need H's short-range action: code running while a
-// stream is being captured into a CUDA graph (cudaMalloc is not a
-// stream-ordered operation and is rejected there), plug-ins whose host
+// at the point where they need H's short-range action: plug-ins whose host
 // framework owns every device byte through its own pool, and real-time loops
 // where an allocation's implicit synchronisation would stall other streams.
 #include "bse_internal.cuh"

@@ -1,9 +1,9 @@
 """The allocation-free short-range entry point against the regular one.
 
 bse_short_range_noalloc serves callers that may not call cudaMalloc where
-they need the short-range term (for instance while their stream is being
-captured into a CUDA graph, or inside a host framework that owns all device
-memory).  It uses a static 2 MiB device array as scratch instead of handle
+they need the short-range term (for instance inside a host framework that
+owns all device memory, or in a real-time loop that cannot afford an
+allocation's synchronisation).  It uses a static 2 MiB device array as scratch instead of handle
 memory.  Here its output is compared with bse_apply_h on a system whose band
 energies, spin-orbit matrix and screened potential are zero, so that H psi is
 exactly the short-range term; both paths run in FP64, so the FP64 parity
