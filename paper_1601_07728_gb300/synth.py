@@ -225,6 +225,137 @@ def make_system_from(cfg: dict, site: int = 0, name: str = "custom", u=None) -> 
                      a_proj=a_proj, m_sr=m_sr, kshift=ks, name=name, meta=dict(cfg))
 
 
+# ---------------------------------------------------------------------------
+# Structured short-range couplings (Sec. 3.2.2): local basis R_{nu,l} Y_{l,m}
+# with 4 radial functions for each l = 0..3 (64 functions), a p core level,
+# and M built from Slater-type radial integrals times Gaunt angular factors,
+# so that only the multipoles allowed by the selection rules appear.
+# ---------------------------------------------------------------------------
+LOCAL_NU, LOCAL_LMAX = 4, 3
+
+
+def wigner3j(j1: int, j2: int, j3: int, m1: int, m2: int, m3: int) -> float:
+    """Wigner 3j symbol for integer arguments (Racah's closed form)."""
+    if m1 + m2 + m3 != 0 or j3 < abs(j1 - j2) or j3 > j1 + j2:
+        return 0.0
+    if abs(m1) > j1 or abs(m2) > j2 or abs(m3) > j3:
+        return 0.0
+    f = math.factorial
+    tri = f(j1 + j2 - j3) * f(j1 - j2 + j3) * f(-j1 + j2 + j3) / f(j1 + j2 + j3 + 1)
+    pre = math.sqrt(tri * f(j1 + m1) * f(j1 - m1) * f(j2 + m2) * f(j2 - m2) * f(j3 + m3) * f(j3 - m3))
+    s = 0.0
+    for tt in range(0, j1 + j2 + j3 + 1):
+        den = (tt, j3 - j2 + tt + m1, j3 - j1 + tt - m2, j1 + j2 - j3 - tt, j1 - tt - m1, j2 - tt + m2)
+        if min(den) < 0:
+            continue
+        prod = 1
+        for d in den:
+            prod *= f(d)
+        s += (-1) ** tt / prod
+    return float((-1) ** (j1 - j2 - m3) * pre * s)
+
+
+def gaunt(l1: int, m1: int, k: int, q: int, l2: int, m2: int) -> float:
+    """<l1 m1| C^k_q |l2 m2> with C^k_q = sqrt(4 pi/(2k+1)) Y_kq."""
+    return ((-1) ** m1 * math.sqrt((2 * l1 + 1) * (2 * l2 + 1)) * wigner3j(l1, k, l2, 0, 0, 0)
+            * wigner3j(l1, k, l2, -m1, q, m2))
+
+
+def local_index(nu: int, l: int, m: int) -> int:
+    """Index p of the local function R_{nu,l} Y_{l,m}: nu slow, then l, then m."""
+    return nu * (LOCAL_LMAX + 1) ** 2 + l * l + (l + m)
+
+
+def local_functions():
+    """[(nu, l, m)] in index order."""
+    return [(nu, l, m) for nu in range(LOCAL_NU) for l in range(LOCAL_LMAX + 1) for m in range(-l, l + 1)]
+
+
+def structured_couplings(rng: np.random.Generator, scale: float = 0.5) -> np.ndarray:
+    """M [(alpha, p)][(alpha', p')] (alpha = 2 (m_c + 1) + s, p = local_index)
+    for a p core hole and the 64 local functions, eV:
+      M = -D + X,  both diagonal in the spin s,
+      D = sum_{k=0,2} F^k_{nu l, nu' l'} sum_q (-1)^q <l m|C^k_q|l' m'> <1 m_c|C^k_-q|1 m_c'>
+      X = sum_k G^k_{nu l, nu' l'} sum_q (-1)^q <l m|C^k_q|1 m_c'> <1 m_c|C^k_-q|l' m'>
+    (direct and exchange multipoles of a scalar two-particle interaction, so
+    M commutes with the total orbital angular momentum).  The radial
+    integrals F^k, G^k are seeded symmetric positive semi-definite matrices
+    over (nu, l) of scale `scale`."""
+    funcs = local_functions()
+    npj = len(funcs)
+    nrad = LOCAL_NU * (LOCAL_LMAX + 1)
+    rad = lambda nu, l: nu * (LOCAL_LMAX + 1) + l
+
+    def radial():
+        b = rng.standard_normal((nrad, nrad))
+        return scale * (b @ b.T) / nrad
+
+    fk = {k: radial() for k in (0, 2)}
+    gk = {k: radial() for k in range(0, LOCAL_LMAX + 2)}
+    mc_list = (-1, 0, 1)
+    orb = np.zeros((3, npj, 3, npj))   # [m_c][p][m_c'][p']
+    for ic, mc in enumerate(mc_list):
+        for p, (nu, l, m) in enumerate(funcs):
+            for jc, mc2 in enumerate(mc_list):
+                for p2, (nu2, l2, m2) in enumerate(funcs):
+                    if m + mc != m2 + mc2:
+                        continue
+                    v = 0.0
+                    for k, f in fk.items():
+                        q = m - m2
+                        v -= f[rad(nu, l), rad(nu2, l2)] * (-1) ** q * gaunt(l, m, k, q, l2, m2) * gaunt(1, mc, k, -q, 1, mc2)
+                    for k, g in gk.items():
+                        q = m - mc2
+                        v += g[rad(nu, l), rad(nu2, l2)] * (-1) ** q * gaunt(l, m, k, q, 1, mc2) * gaunt(1, mc, k, -q, l2, m2)
+                    orb[ic, p, jc, p2] = v
+    M = np.zeros((6 * npj, 6 * npj), dtype=np.complex128)
+    for ic, mc in enumerate(mc_list):
+        for jc, mc2 in enumerate(mc_list):
+            for s in (0, 1):
+                a, a2 = 2 * (mc + 1) + s, 2 * (mc2 + 1) + s
+                M[a * npj:(a + 1) * npj, a2 * npj:(a2 + 1) * npj] = orb[ic, :, jc, :]
+    return M
+
+
+def dipole_start_vectors(a_proj: np.ndarray, qs=(-1, 0, 1), seed: int = 0) -> np.ndarray:
+    """Start vectors b_q shaped by the dipole operator from the p core level
+    into the local basis (Sec. 2, the x-ray matrix elements), one per
+    polarisation component q:  b_q(alpha = (m_c, s), n, k) =
+    sum_{nu, l in (0, 2), m} d_{nu l} <l m|C^1_q|1 m_c> conj(A^{nu l m}_{nk}),
+    d_{nu l} seeded radial dipole integrals; each b_q normalised to 1.
+    a_proj [64][Nk][Nb] -> b [len(qs)][6 * Nk * Nb]."""
+    rng = np.random.default_rng([3, 7, int(seed)])
+    d = rng.uniform(0.5, 1.5, size=(LOCAL_NU, LOCAL_LMAX + 1))
+    npj, nk, nb = a_proj.shape
+    out = np.zeros((len(qs), 6, nk * nb), dtype=np.complex128)
+    a2 = a_proj.reshape(npj, nk * nb)
+    for iq, q in enumerate(qs):
+        for mc in (-1, 0, 1):
+            acc = np.zeros(nk * nb, dtype=np.complex128)
+            for nu in range(LOCAL_NU):
+                for l in (0, 2):
+                    for m in range(-l, l + 1):
+                        gq = gaunt(l, m, 1, q, 1, mc)
+                        if gq != 0.0:
+                            acc += d[nu, l] * gq * np.conj(a2[local_index(nu, l, m)])
+            for s in (0, 1):
+                out[iq, 2 * (mc + 1) + s] = acc
+        out[iq] /= np.linalg.norm(out[iq])
+    return out.reshape(len(qs), -1)
+
+
+def structured_system(cfg: dict, site: int = 0, name: str = "structured") -> BSESystem:
+    """make_system_from with the 64-function local basis and structured M
+    (structured_couplings); requires 6 core states."""
+    c = dict(cfg)
+    c["n_proj"] = LOCAL_NU * (LOCAL_LMAX + 1) ** 2
+    s = make_system_from(c, site=site, name=name)
+    if s.n_alpha != 6:
+        raise ValueError("structured couplings need the 6 states of a p core level")
+    s.m_sr = structured_couplings(rng_for(int(c.get("id", 99)), site, STREAM_M), float(c.get("m_scale", 0.5)))
+    return s
+
+
 def batched_site_config(site: int) -> dict:
     """Shape of one site of the many-site workload: k mesh n^3 with
     n ~ U{4..8}, grid m^3 with m ~ U{12..20}, Nb ~ U{32..256}, and 1 or 6 core

@@ -1,0 +1,109 @@
+"""Pins of the structured short-range inputs (Sec. 3.2.2): Wigner 3j and
+Gaunt factors against closed forms and orthogonality, the Slater x Gaunt
+coupling matrix M (Hermitian, spin-diagonal, invariant under total orbital
+rotations of electron and hole) and the dipole-shaped start vectors (only
+the s and d local functions contribute from a p core level)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_07728_gb300 import synth as S
+
+
+def test_wigner3j_closed_forms_and_orthogonality():
+    assert S.wigner3j(1, 1, 0, 0, 0, 0) == pytest.approx(-1 / math.sqrt(3), abs=1e-15)
+    assert S.wigner3j(1, 1, 2, 0, 0, 0) == pytest.approx(math.sqrt(2 / 15), abs=1e-15)
+    assert S.wigner3j(2, 2, 0, 1, -1, 0) == pytest.approx(-1 / math.sqrt(5), abs=1e-15)
+    assert S.wigner3j(1, 1, 1, 0, 0, 0) == 0.0                  # odd sum with all m = 0
+    # sum_{m1 m2} (2 j3 + 1) (j1 j2 j3; m1 m2 m3) (j1 j2 j3'; m1 m2 m3') = delta delta
+    for j1, j2 in ((1, 2), (2, 3), (1, 1)):
+        for j3 in range(abs(j1 - j2), j1 + j2 + 1):
+            for j3p in range(abs(j1 - j2), j1 + j2 + 1):
+                for m3 in range(-min(j3, j3p), min(j3, j3p) + 1):
+                    s = sum((2 * j3 + 1) * S.wigner3j(j1, j2, j3, m1, m2, m3) * S.wigner3j(j1, j2, j3p, m1, m2, m3)
+                            for m1 in range(-j1, j1 + 1) for m2 in range(-j2, j2 + 1))
+                    assert s == pytest.approx(1.0 if j3 == j3p else 0.0, abs=1e-12)
+
+
+def test_gaunt_identity_parity_and_dipole():
+    for l in range(4):
+        for m in range(-l, l + 1):
+            for m2 in range(-l, l + 1):
+                assert S.gaunt(l, m, 0, 0, l, m2) == pytest.approx(1.0 if m == m2 else 0.0, abs=1e-14)
+    assert S.gaunt(1, 0, 1, 0, 1, 0) == 0.0                     # parity: l + k + l' odd
+    assert S.gaunt(2, 1, 2, 1, 1, 0) == 0.0                     # parity again
+    assert S.gaunt(0, 0, 1, 0, 1, 0) ** 2 == pytest.approx(1 / 3, abs=1e-14)   # |<s|C^1_0|p_0>|^2
+    # sum_{q, m} |<l m|C^k_q|l' m'>|^2 = (2l + 1) (l k l'; 0 0 0)^2 for every m' (3j
+    # orthogonality): p -> d dipole strength 5 * 2/15 = 2/3, p -> s 1/3, from each core m
+    for mc in (-1, 0, 1):
+        tot_d = sum(S.gaunt(2, m, 1, q, 1, mc) ** 2 for q in (-1, 0, 1) for m in range(-2, 3))
+        tot_s = sum(S.gaunt(0, 0, 1, q, 1, mc) ** 2 for q in (-1, 0, 1))
+        assert tot_d == pytest.approx(2 / 3, abs=1e-12)
+        assert tot_s == pytest.approx(1 / 3, abs=1e-12)
+
+
+@pytest.fixture(scope="module")
+def mstruct():
+    return S.structured_couplings(np.random.default_rng(5))
+
+
+def _orbital_block(M):
+    npj = len(S.local_functions())
+    idx = [2 * (mc + 1) * npj + p for mc in (-1, 0, 1) for p in range(npj)]   # spin up
+    return M[np.ix_(idx, idx)]
+
+
+def _total_lplus():
+    funcs = S.local_functions()
+    npj = len(funcs)
+    le = np.zeros((npj, npj))
+    for p, (nu, l, m) in enumerate(funcs):
+        if m < l:
+            le[S.local_index(nu, l, m + 1), p] = math.sqrt(l * (l + 1) - m * (m + 1))
+    lh = np.zeros((3, 3))
+    for i, mc in enumerate((-1, 0, 1)):
+        if mc < 1:
+            lh[i + 1, i] = math.sqrt(2 - mc * (mc + 1))
+    return np.kron(lh, np.eye(npj)) + np.kron(np.eye(3), le)
+
+
+def test_coupling_matrix_hermitian_spin_diagonal_and_rotation_invariant(mstruct):
+    M = mstruct
+    npj = len(S.local_functions())
+    assert np.abs(M - M.conj().T).max() < 1e-14
+    for a in range(6):
+        for b in range(6):
+            if a % 2 != b % 2:   # different spin
+                assert np.abs(M[a * npj:(a + 1) * npj, b * npj:(b + 1) * npj]).max() == 0.0
+    orb = _orbital_block(M)
+    lp = _total_lplus()
+    lz = np.diag([mc + m for mc in (-1, 0, 1) for (_, _, m) in S.local_functions()])
+    assert np.abs(orb @ lz - lz @ orb).max() < 1e-12
+    assert np.abs(orb @ lp - lp @ orb).max() < 1e-12 * max(1.0, np.abs(orb).max())
+    assert np.abs(orb).max() > 0.05                              # not trivially zero
+
+
+def test_planted_phase_error_breaks_rotation_invariance(monkeypatch):
+    real = S.gaunt
+    monkeypatch.setattr(S, "gaunt", lambda l1, m1, k, q, l2, m2: real(l1, m1, k, q, l2, m2) * (-1) ** m1)
+    orb = _orbital_block(S.structured_couplings(np.random.default_rng(5)))
+    lp = _total_lplus()
+    assert np.abs(orb @ lp - lp @ orb).max() > 1e-3
+
+
+def test_dipole_vectors_see_only_s_and_d_functions():
+    rng = np.random.default_rng(9)
+    npj = len(S.local_functions())
+    a = S.complex_normal(rng, (npj, 2, 5))
+    b = S.dipole_start_vectors(a)
+    a2 = a.copy()
+    for p, (nu, l, m) in enumerate(S.local_functions()):
+        if l in (1, 3):
+            a2[p] = S.complex_normal(rng, (2, 5))
+    assert np.allclose(S.dipole_start_vectors(a2), b, atol=1e-14)
+    assert b.shape == (3, 6 * 10)
+    assert np.allclose(np.linalg.norm(b, axis=1), 1.0)
+    # spin-independent: both spin copies of each core m carry the same amplitudes
+    bb = b.reshape(3, 6, 10)
+    assert np.allclose(bb[:, 0::2], bb[:, 1::2])
