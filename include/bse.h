@@ -238,6 +238,19 @@ bse_status bse_gmres_set_mlp(bse_handle* h, bse_mlp* m);
  * preconditioner. */
 bse_status bse_jacobi_diag(bse_handle* h, double* diag);
 
+/* Projection of the Bloch functions onto the local basis around the
+ * absorbing atom (Sec. 3.2.2, the expansion of phi_nk near the atom in
+ * R_{nu,l} Y_{l,m}), the set-up step that produces a_proj for bse_setup:
+ *   a[p][k][n] = dv * sum_x conj(f[p][x]) e^{i k.x} u[k][x][n],
+ * u [Nk][Nx][Nb] (periodic parts, as for bse_setup), f [n_proj][Nx] the local
+ * functions sampled on the cell's grid (zero outside their radius), k and x
+ * indexed as in bse_setup, kshift [3] or NULL, dv the volume per grid point;
+ * a [n_proj][Nk][Nb].  All complex128, host or device; FP64 arithmetic.
+ * Work runs on `stream` (NULL: legacy default) and the call returns when a is
+ * written.  Allocates staging copies of host arrays. */
+bse_status bse_local_projection(const bse_c128* u, const int* nk, const int* nx, int n_bands, const double* kshift,
+                                const bse_c128* f, int n_proj, double dv, bse_c128* a, void* stream);
+
 /* Short-range (local direct + exchange) term alone, out = (A (x) I)^H M (A (x) I) psi,
  * computed without allocating any memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need

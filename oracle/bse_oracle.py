@@ -77,6 +77,18 @@ def _shape(s):
 # H psi: literal Algorithm 1 (tiny inputs only)
 # ----------------------------------------------------------------------------
 
+def local_projection(u, nk, nx, f, dv, kshift=(0.0, 0.0, 0.0)):
+    """Projection of the Bloch functions onto the local basis (Sec. 3.2.2):
+    A[p][k][n] = dv sum_x conj(f_p(x)) e^{i k.x} u_nk(x); u [Nk][Nx][Nb],
+    f [Np][Nx] -> A [Np][Nk][Nb]."""
+    ph = kx_phase(nk, nx, kshift)
+    fc = np.conj(f)
+    a = np.empty((f.shape[0], u.shape[0], u.shape[2]), dtype=np.complex128)
+    for k in range(u.shape[0]):
+        a[:, k, :] = dv * (fc @ (ph[k][:, None] * u[k]))
+    return a
+
+
 def apply_w0_loop(s, psi):
     """W_0 psi by Algorithm 1 as printed: for each x and alpha, build phi(k),
     transform k->R with an explicit sum, multiply by W(x, R), transform back,

@@ -26,7 +26,7 @@ EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", 
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
            "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc",
            "bse_mlp_n_params", "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_params", "bse_mlp_outputs",
-           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles"]
+           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection"]
 KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
 
 
@@ -117,6 +117,8 @@ def lib():
     L.bse_autotune.restype = ci
     L.bse_set_tiles.argtypes = [vp, ci, ci]
     L.bse_set_tiles.restype = ci
+    L.bse_local_projection.argtypes = [vp, vp, vp, ci, vp, vp, ci, cd, vp, vp]
+    L.bse_local_projection.restype = ci
     _LIB = L
     return L
 
@@ -373,6 +375,22 @@ def _chk(st):
 
 def attach_mlp(sysg, mlp):
     sysg._check(lib().bse_gmres_set_mlp(sysg.h, mlp.h if mlp is not None else None))
+
+
+def local_projection(u, nk, nx, f, dv, kshift=(0.0, 0.0, 0.0), stream=None):
+    """bse_local_projection: a [Np][Nk][Nb] = dv sum_x conj(f_p(x)) e^{ik.x} u_nk(x) (host arrays in and out)."""
+    u = np.ascontiguousarray(u, dtype=np.complex128)
+    f = np.ascontiguousarray(f, dtype=np.complex128)
+    nkt, nxt, nb = u.shape
+    npj = f.shape[0]
+    a = np.zeros((npj, nkt, nb), dtype=np.complex128)
+    nk_a = (ctypes.c_int * 3)(*nk)
+    nx_a = (ctypes.c_int * 3)(*nx)
+    ks = (ctypes.c_double * 3)(*kshift)
+    st = lib().bse_local_projection(u.ctypes.data, nk_a, nx_a, nb, ks, f.ctypes.data, npj, float(dv), a.ctypes.data,
+                                    stream)
+    _chk(st)
+    return a
 
 
 def short_range_noalloc(a_proj, m_sr, psi, out, n_alpha, stream=None):

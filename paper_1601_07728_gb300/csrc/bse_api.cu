@@ -322,6 +322,26 @@ bse_status bse_cf_spectrum(const double* a, const double* bcoef, const int* step
   return BSE_OK;
 }
 
+bse_status bse_local_projection(const bse_c128* u, const int* nk, const int* nx, int n_bands, const double* kshift,
+                                const bse_c128* f, int n_proj, double dv, bse_c128* a, void* stream) {
+  if (!u || !nk || !nx || !f || !a || n_bands < 1 || n_proj < 1 || n_proj > 4096) return BSE_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (nk[d] < 1 || nk[d] > BSE_MAX_NK_AXIS || nx[d] < 1) return BSE_ERR_INVALID_ARG;
+  const size_t nkt = (size_t)nk[0] * nk[1] * nk[2], nxt = (size_t)nx[0] * nx[1] * nx[2];
+  if ((size_t)n_bands > nxt) return BSE_ERR_INVALID_ARG;
+  bse_handle tmp;   // error sink
+  tmp.stream = (cudaStream_t)stream;
+  Staged su, sf, sa;
+  TRY(stage_in(&tmp, su, u, nkt * nxt * n_bands * sizeof(double2), true, "u"));
+  TRY(stage_in(&tmp, sf, f, (size_t)n_proj * nxt * sizeof(double2), true, "f"));
+  TRY(stage_in(&tmp, sa, a, (size_t)n_proj * nkt * n_bands * sizeof(double2), false, "a"));
+  TRY(bse_local_projection_device((const double2*)su.dev, nk, nx, n_bands, kshift, (const double2*)sf.dev, n_proj, dv,
+                                  (double2*)sa.dev, tmp.stream));
+  TRY(stage_out(&tmp, sa, a, (size_t)n_proj * nkt * n_bands * sizeof(double2), "a copy-out"));
+  TRY(bse_cuda_check(&tmp, cudaStreamSynchronize(tmp.stream), "local projection sync"));
+  return BSE_OK;
+}
+
 bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_z, double rtol, int restart,
                      int max_iter, int precond, bse_c128* x, int* iters, double* rel_resid) {
   if (!h) return BSE_ERR_INVALID_ARG;

@@ -174,6 +174,9 @@ struct bse_operand_out {
   float2* psi_f = nullptr;
   int nk = 0, nb = 0, na = 0, kp = 0, nnmax = 0;
 };
+// A[p][k][n] = dv sum_x conj(f_p(x)) e^{ik.x} u_nk(x) on device arrays (k_local.cu)
+bse_status bse_local_projection_device(const double2* u, const int* nk, const int* nx, int nb, const double* kshift,
+                                       const double2* f, int np, double dv, double2* a, cudaStream_t st);
 // the tensor-core form's operand buffers of a handle (k_tc.cu)
 bse_operand_out bse_tc_operand(const bse_handle* h);
 

@@ -344,6 +344,58 @@ def dipole_start_vectors(a_proj: np.ndarray, qs=(-1, 0, 1), seed: int = 0) -> np
     return out.reshape(len(qs), -1)
 
 
+def spherical_harmonic(l: int, m: int, theta: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """Y_{l,m}(theta, phi), orthonormal on the sphere, Condon-Shortley phase
+    (associated Legendre functions by the standard upward recurrence)."""
+    am = abs(m)
+    x = np.cos(theta)
+    somx2 = np.sqrt(np.maximum(0.0, 1.0 - x * x))
+    pmm = np.ones_like(x)
+    fact = 1.0
+    for _ in range(am):
+        pmm = -pmm * fact * somx2
+        fact += 2.0
+    if l == am:
+        plm = pmm
+    else:
+        pmm1 = x * (2 * am + 1) * pmm
+        if l == am + 1:
+            plm = pmm1
+        else:
+            for ll in range(am + 2, l + 1):
+                pll = (x * (2 * ll - 1) * pmm1 - (ll + am - 1) * pmm) / (ll - am)
+                pmm, pmm1 = pmm1, pll
+            plm = pmm1
+    norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+    y = norm * plm * np.exp(1j * am * phi)
+    if m < 0:
+        y = (-1) ** am * np.conj(y)
+    return y
+
+
+def local_functions_on_grid(nx, cell: float, rc: float, seed: int = 0) -> np.ndarray:
+    """The 64 local functions f_p(x) = R_{nu,l}(r) Y_{l,m}(r^) sampled on the
+    cell's grid x_d = j_d a / n_x_d, with r the minimum-image distance to the
+    absorbing atom at the origin and f = 0 for r >= rc; radial functions
+    R_{nu,l}(r) = r^l exp(-(r / s_nu)^2) with seeded widths s_nu < rc.
+    Index order p = local_index(nu, l, m).  Returns [64][Nx] complex128."""
+    rng = np.random.default_rng([3, 11, int(seed)])
+    widths = np.sort(rng.uniform(0.15 * rc, 0.6 * rc, size=LOCAL_NU))
+    j = np.stack(np.meshgrid(*[np.arange(n) for n in nx], indexing="ij"), -1).reshape(-1, 3)
+    frac = j / np.asarray(nx, dtype=np.float64)
+    frac = frac - np.round(frac)          # minimum image in the cell
+    xyz = frac * cell
+    r = np.linalg.norm(xyz, axis=1)
+    theta = np.arccos(np.clip(np.where(r > 0, xyz[:, 2] / np.maximum(r, 1e-300), 1.0), -1.0, 1.0))
+    phi = np.arctan2(xyz[:, 1], xyz[:, 0])
+    inside = r < rc
+    out = np.zeros((LOCAL_NU * (LOCAL_LMAX + 1) ** 2, len(r)), dtype=np.complex128)
+    for nu, l, m in local_functions():
+        rad = r ** l * np.exp(-(r / widths[nu]) ** 2)
+        out[local_index(nu, l, m)] = np.where(inside, rad * spherical_harmonic(l, m, theta, phi), 0.0)
+    return out
+
+
 def structured_system(cfg: dict, site: int = 0, name: str = "structured") -> BSESystem:
     """make_system_from with the 64-function local basis and structured M
     (structured_couplings); requires 6 core states."""

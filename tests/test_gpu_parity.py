@@ -104,6 +104,23 @@ def test_autotune_choice_keeps_parity():
     assert bse.System(s, precision="fp64").autotune() == (0, 0)
 
 
+@pytest.mark.parametrize("shape", [((2, 2, 2), (6, 6, 6), 20, (0.0, 0.0, 0.0)),
+                                   ((4, 4, 4), (12, 12, 12), 40, (0.5, 0.25, 0.0)),
+                                   ((3, 2, 5), (7, 5, 6), 33, (0.0, 0.5, 0.0))])
+def test_local_projection_matches_oracle(shape):
+    """Set-up projection onto the 64 local functions R_{nu,l} Y_{l,m} (Sec.
+    3.2.2), FP64 on the GPU, against the oracle's definition; cubic, shifted
+    and ragged meshes, tiles not filled by the band and projector counts."""
+    nk, nx, nb, ks = shape
+    s = S.make_system_from(dict(id=960, n_alpha=1, nk=nk, n_bands=nb, nx=nx, cell=7.4, eps=5.0, n_proj=0,
+                                kshift=ks), 0)
+    f = S.local_functions_on_grid(s.nx, s.cell, 2.5)
+    dv = s.cell ** 3 / s.n_x
+    a = bse.local_projection(s.u, s.nk, s.nx, f, dv, s.kshift)
+    ref = O.local_projection(s.u, s.nk, s.nx, f, dv, s.kshift)
+    assert rel(a, ref) < 1e-12
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
 def test_structured_multiplets_match_oracle(prec):
     """The 64-function local basis (4 radial functions for each l <= 3) with

@@ -408,3 +408,24 @@ def test_golden_haydock_regression(kedge, reorth, tol):
     assert nd == 100
     assert np.allclose(a, g[:100, 1], rtol=tol, atol=tol)
     assert np.allclose(bb, g[:, 2], rtol=tol, atol=tol)
+
+
+def test_local_projection_against_loop_and_orthonormal_columns():
+    """A[p][k][n] = dv sum_x conj(f_p(x)) e^{ik.x} u_nk(x): the vectorised
+    oracle against an explicit loop, and with f_p = e^{ik0.x} u_{n0 k0} / dv
+    (shifted mesh) the orthonormal columns give A[p][k0][n] = delta_{n n0}."""
+    s = S.tiny_system(71, n_alpha=1, nk=(2, 1, 2), n_bands=3, nx=(3, 2, 2), n_proj=0, kshift=(0.5, 0.0, 0.25))
+    rng = np.random.default_rng(2)
+    f = S.complex_normal(rng, (4, s.n_x))
+    dv = 0.37
+    a = O.local_projection(s.u, s.nk, s.nx, f, dv, s.kshift)
+    ph = O.kx_phase(s.nk, s.nx, s.kshift)
+    for p in range(4):
+        for k in range(s.n_k):
+            for n in range(s.n_bands):
+                ref = dv * sum(np.conj(f[p, x]) * ph[k, x] * s.u[k, x, n] for x in range(s.n_x))
+                assert abs(a[p, k, n] - ref) < 1e-13
+    k0, n0 = 3, 1
+    f2 = (ph[k0] * s.u[k0, :, n0])[None, :] / dv
+    a2 = O.local_projection(s.u, s.nk, s.nx, f2, dv, s.kshift)
+    assert np.allclose(a2[0, k0], np.eye(s.n_bands)[n0], atol=1e-13)

@@ -107,3 +107,39 @@ def test_dipole_vectors_see_only_s_and_d_functions():
     # spin-independent: both spin copies of each core m carry the same amplitudes
     bb = b.reshape(3, 6, 10)
     assert np.allclose(bb[:, 0::2], bb[:, 1::2])
+
+
+def test_spherical_harmonics_closed_forms():
+    rng = np.random.default_rng(3)
+    th = rng.uniform(0, np.pi, 50)
+    ph = rng.uniform(-np.pi, np.pi, 50)
+    assert np.allclose(S.spherical_harmonic(0, 0, th, ph), 0.5 / math.sqrt(math.pi))
+    assert np.allclose(S.spherical_harmonic(1, 0, th, ph), math.sqrt(3 / (4 * math.pi)) * np.cos(th))
+    assert np.allclose(S.spherical_harmonic(1, 1, th, ph), -math.sqrt(3 / (8 * math.pi)) * np.sin(th) * np.exp(1j * ph))
+    assert np.allclose(S.spherical_harmonic(1, -1, th, ph), math.sqrt(3 / (8 * math.pi)) * np.sin(th) * np.exp(-1j * ph))
+    assert np.allclose(S.spherical_harmonic(2, 0, th, ph),
+                       math.sqrt(5 / (16 * math.pi)) * (3 * np.cos(th) ** 2 - 1))
+    assert np.allclose(S.spherical_harmonic(3, 3, th, ph),
+                       -math.sqrt(35 / (64 * math.pi)) * np.sin(th) ** 3 * np.exp(3j * ph))
+
+
+def test_spherical_harmonics_orthonormal_on_a_quadrature():
+    """Gauss-Legendre in cos(theta) x uniform phi integrates products of Y_lm
+    (l <= 3) exactly."""
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    phis = np.linspace(0, 2 * np.pi, 16, endpoint=False)
+    th = np.repeat(np.arccos(xg), len(phis))
+    ph = np.tile(phis, len(xg))
+    w = np.repeat(wg, len(phis)) * (2 * np.pi / len(phis))
+    ys = [S.spherical_harmonic(l, m, th, ph) for l in range(4) for m in range(-l, l + 1)]
+    g = np.array([[np.sum(w * np.conj(a) * b) for b in ys] for a in ys])
+    assert np.abs(g - np.eye(16)).max() < 1e-12
+
+
+def test_local_functions_vanish_outside_their_radius():
+    f = S.local_functions_on_grid((6, 6, 6), 7.4, 2.0)
+    assert f.shape == (64, 216)
+    j = np.stack(np.meshgrid(*[np.arange(6)] * 3, indexing="ij"), -1).reshape(-1, 3) / 6.0
+    r = np.linalg.norm((j - np.round(j)) * 7.4, axis=1)
+    assert np.abs(f[:, r >= 2.0]).max() == 0.0
+    assert np.abs(f[:, r < 2.0]).max() > 0.0
