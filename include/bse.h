@@ -251,6 +251,21 @@ bse_status bse_jacobi_diag(bse_handle* h, double* diag);
 bse_status bse_local_projection(const bse_c128* u, const int* nk, const int* nx, int n_bands, const double* kshift,
                                 const bse_c128* f, int n_proj, double dv, bse_c128* a, void* stream);
 
+/* Screening stage (Sec. 3.3): the Green's function on the real-space grid
+ * around the core hole along the imaginary axis and the static RPA response,
+ *   G_j(r, r') = sum_K psi[r][K] conj(psi[r'][K]) / (mu + i t_j - eps[K]),
+ *   chi0(r, r') = (1/2 pi) sum_j w_j G_j(r, r') G_j(r', r)
+ * (the frequency integral of chi^0 along omega' = mu + i t with quadrature
+ * nodes t [n_t] and weights w [n_t]); K = (n, k) runs over the n_states
+ * band/k states.  psi [n_r][n_states] (the Bloch functions on the grid), eps
+ * [n_states] eV, chi0 [n_r][n_r]; green [n_t][n_r][n_r] receives the G_j or
+ * may be NULL.  Complex128 / FP64, host or device; work on `stream` (NULL:
+ * legacy default), returns when the outputs are written.  Allocates staging
+ * and the G_j scratch. */
+bse_status bse_screening_chi0(const bse_c128* psi, const double* eps, int n_r, int n_states, double mu,
+                              const double* t, const double* w, int n_t, bse_c128* green, bse_c128* chi0,
+                              void* stream);
+
 /* Short-range (local direct + exchange) term alone, out = (A (x) I)^H M (A (x) I) psi,
  * computed without allocating any memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need

@@ -89,6 +89,19 @@ def local_projection(u, nk, nx, f, dv, kshift=(0.0, 0.0, 0.0)):
     return a
 
 
+def screening_green(psi, eps, mu, t):
+    """G_j(r, r') = sum_K psi(r, K) conj(psi(r', K)) / (mu + i t_j - eps_K)
+    (the Green's function of Sec. 3.3 on the grid, imaginary frequencies)."""
+    return np.stack([(psi / (mu + 1j * tj - eps)[None, :]) @ psi.conj().T for tj in t])
+
+
+def screening_chi0(psi, eps, mu, t, w):
+    """chi0(r, r') = (1/2 pi) sum_j w_j G_j(r, r') G_j(r', r): the frequency
+    integral of the RPA chi^0 (Sec. 3.3) along omega' = mu + i t, static."""
+    g = screening_green(psi, eps, mu, t)
+    return np.einsum("j,jrc,jcr->rc", np.asarray(w, dtype=np.float64), g, g) / TWO_PI
+
+
 def apply_w0_loop(s, psi):
     """W_0 psi by Algorithm 1 as printed: for each x and alpha, build phi(k),
     transform k->R with an explicit sum, multiply by W(x, R), transform back,

@@ -26,7 +26,7 @@ EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", 
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
            "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc",
            "bse_mlp_n_params", "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_params", "bse_mlp_outputs",
-           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection"]
+           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0"]
 KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
 
 
@@ -119,6 +119,8 @@ def lib():
     L.bse_set_tiles.restype = ci
     L.bse_local_projection.argtypes = [vp, vp, vp, ci, vp, vp, ci, cd, vp, vp]
     L.bse_local_projection.restype = ci
+    L.bse_screening_chi0.argtypes = [vp, vp, ci, ci, cd, vp, vp, ci, vp, vp, vp]
+    L.bse_screening_chi0.restype = ci
     _LIB = L
     return L
 
@@ -391,6 +393,21 @@ def local_projection(u, nk, nx, f, dv, kshift=(0.0, 0.0, 0.0), stream=None):
                                     stream)
     _chk(st)
     return a
+
+
+def screening_chi0(psi, eps, mu, t, w, want_green=False, stream=None):
+    """bse_screening_chi0 on host arrays: returns chi0 [R][R] (and G [n_t][R][R] when want_green)."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    nr, ns = psi.shape
+    chi = np.zeros((nr, nr), dtype=np.complex128)
+    g = np.zeros((t.size, nr, nr), dtype=np.complex128) if want_green else None
+    st = lib().bse_screening_chi0(psi.ctypes.data, eps.ctypes.data, nr, ns, float(mu), t.ctypes.data, w.ctypes.data,
+                                  t.size, g.ctypes.data if g is not None else None, chi.ctypes.data, stream)
+    _chk(st)
+    return (chi, g) if want_green else chi
 
 
 def short_range_noalloc(a_proj, m_sr, psi, out, n_alpha, stream=None):

@@ -342,6 +342,32 @@ bse_status bse_local_projection(const bse_c128* u, const int* nk, const int* nx,
   return BSE_OK;
 }
 
+bse_status bse_screening_chi0(const bse_c128* psi, const double* eps, int n_r, int n_states, double mu,
+                              const double* t, const double* w, int n_t, bse_c128* green, bse_c128* chi0,
+                              void* stream) {
+  if (!psi || !eps || !t || !w || !chi0 || n_r < 1 || n_states < 1 || n_t < 1) return BSE_ERR_INVALID_ARG;
+  bse_handle tmp;   // error sink
+  tmp.stream = (cudaStream_t)stream;
+  const size_t nrr = (size_t)n_r * n_r;
+  Staged sp, se, st_, sw, sc, sg;
+  TRY(stage_in(&tmp, sp, psi, (size_t)n_r * n_states * sizeof(double2), true, "psi"));
+  TRY(stage_in(&tmp, se, eps, (size_t)n_states * sizeof(double), true, "eps"));
+  TRY(stage_in(&tmp, st_, t, (size_t)n_t * sizeof(double), true, "t"));
+  TRY(stage_in(&tmp, sw, w, (size_t)n_t * sizeof(double), true, "w"));
+  TRY(stage_in(&tmp, sc, chi0, nrr * sizeof(double2), false, "chi0"));
+  if (green) {
+    TRY(stage_in(&tmp, sg, green, (size_t)n_t * nrr * sizeof(double2), false, "green"));
+  } else {
+    TRY(stage_in(&tmp, sg, nullptr, (size_t)n_t * nrr * sizeof(double2), false, "green (scratch)"));
+  }
+  TRY(bse_screening_device((const double2*)sp.dev, (const double*)se.dev, n_r, n_states, mu, (const double*)st_.dev,
+                           (const double*)sw.dev, n_t, (double2*)sg.dev, (double2*)sc.dev, tmp.stream));
+  if (green) TRY(stage_out(&tmp, sg, green, (size_t)n_t * nrr * sizeof(double2), "green copy-out"));
+  TRY(stage_out(&tmp, sc, chi0, nrr * sizeof(double2), "chi0 copy-out"));
+  TRY(bse_cuda_check(&tmp, cudaStreamSynchronize(tmp.stream), "screening sync"));
+  return BSE_OK;
+}
+
 bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_z, double rtol, int restart,
                      int max_iter, int precond, bse_c128* x, int* iters, double* rel_resid) {
   if (!h) return BSE_ERR_INVALID_ARG;

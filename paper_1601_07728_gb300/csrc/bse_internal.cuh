@@ -177,6 +177,9 @@ struct bse_operand_out {
 // A[p][k][n] = dv sum_x conj(f_p(x)) e^{ik.x} u_nk(x) on device arrays (k_local.cu)
 bse_status bse_local_projection_device(const double2* u, const int* nk, const int* nx, int nb, const double* kshift,
                                        const double2* f, int np, double dv, double2* a, cudaStream_t st);
+// screening: G_j = psi diag(1/(mu + i t_j - eps)) psi^H for all j, chi0 from them (k_screen.cu)
+bse_status bse_screening_device(const double2* psi, const double* eps, int nr, int nkk, double mu, const double* t,
+                                const double* w, int nt, double2* G, double2* chi, cudaStream_t st);
 // the tensor-core form's operand buffers of a handle (k_tc.cu)
 bse_operand_out bse_tc_operand(const bse_handle* h);
 

@@ -396,6 +396,25 @@ def local_functions_on_grid(nx, cell: float, rc: float, seed: int = 0) -> np.nda
     return out
 
 
+def imag_axis_quadrature(n: int, scale: float = 5.0):
+    """Nodes t and weights w for integrals over t in (-inf, inf): Gauss-Legendre
+    in u on (-1, 1) with t = scale * tan(pi u / 2)."""
+    u, wu = np.polynomial.legendre.leggauss(n)
+    t = scale * np.tan(0.5 * np.pi * u)
+    w = wu * scale * 0.5 * np.pi / np.cos(0.5 * np.pi * u) ** 2
+    return t, w
+
+
+def screening_grid_states(n_r: int, n_states: int, seed: int = 0, e_range=(-10.0, 10.0)):
+    """Bloch functions on a real-space grid around the core hole (n_r points,
+    e.g. 36 angular x 25 radial = 900) for n_states band/k states: seeded
+    complex normal values, and band energies uniform in e_range (eV)."""
+    rng = rng_for(5, int(seed), STREAM_U)
+    psi = complex_normal(rng, (n_r, n_states)) / math.sqrt(n_r)
+    eps = rng_for(5, int(seed), STREAM_E).uniform(e_range[0], e_range[1], size=n_states)
+    return psi, eps
+
+
 def structured_system(cfg: dict, site: int = 0, name: str = "structured") -> BSESystem:
     """make_system_from with the 64-function local basis and structured M
     (structured_couplings); requires 6 core states."""

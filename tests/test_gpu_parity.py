@@ -104,6 +104,21 @@ def test_autotune_choice_keeps_parity():
     assert bse.System(s, precision="fp64").autotune() == (0, 0)
 
 
+@pytest.mark.parametrize("shape", [(900, 512, 16), (37, 45, 6)])
+def test_screening_chi0_matches_oracle(shape):
+    """Screening stage (Sec. 3.3) on the 900-point grid around the core hole
+    and on a ragged small case: the Green's functions at every imaginary
+    frequency and the static chi0 against the oracle, FP64."""
+    nr, ns, nt = shape
+    psi, eps = S.screening_grid_states(nr, ns, seed=nr)
+    es = np.sort(eps)
+    mu = float(es[ns // 2 - 1] + es[ns // 2]) / 2   # between two band energies
+    t, w = S.imag_axis_quadrature(nt, scale=8.0)
+    chi, g = bse.screening_chi0(psi, eps, mu, t, w, want_green=True)
+    assert rel(g, O.screening_green(psi, eps, mu, t)) < 1e-12
+    assert rel(chi, O.screening_chi0(psi, eps, mu, t, w)) < 1e-12
+
+
 @pytest.mark.parametrize("shape", [((2, 2, 2), (6, 6, 6), 20, (0.0, 0.0, 0.0)),
                                    ((4, 4, 4), (12, 12, 12), 40, (0.5, 0.25, 0.0)),
                                    ((3, 2, 5), (7, 5, 6), 33, (0.0, 0.5, 0.0))])

@@ -429,3 +429,27 @@ def test_local_projection_against_loop_and_orthonormal_columns():
     f2 = (ph[k0] * s.u[k0, :, n0])[None, :] / dv
     a2 = O.local_projection(s.u, s.nk, s.nx, f2, dv, s.kshift)
     assert np.allclose(a2[0, k0], np.eye(s.n_bands)[n0], atol=1e-13)
+
+
+def test_screening_chi0_equals_static_lindhard_form():
+    """The imaginary-axis integral of G G (Sec. 3.3) against its closed form:
+    (1/2 pi) int dt / ((a + i t)(b + i t)) = 1/(b - a) when a > 0 > b, 0 when
+    a and b have the same sign, so chi0(r, r') = sum_{K occ, L empty}
+    [psi_K(r) psi_K*(r') psi_L(r') psi_L*(r) + (K <-> L)] / (eps_K - eps_L)."""
+    psi, eps = S.screening_grid_states(7, 6, seed=1)
+    mu = float(np.sort(eps)[2] + np.sort(eps)[3]) / 2   # three states below mu, three above
+    t, w = S.imag_axis_quadrature(600, scale=8.0)
+    chi = O.screening_chi0(psi, eps, mu, t, w)
+    ref = np.zeros((7, 7), dtype=np.complex128)
+    for K in range(6):
+        for L in range(6):
+            if eps[K] < mu < eps[L]:
+                pk, pl = psi[:, K], psi[:, L]
+                term = (np.outer(pk, pk.conj()) * np.outer(pl, pl.conj()).T
+                        + np.outer(pl, pl.conj()) * np.outer(pk, pk.conj()).T) / (eps[K] - eps[L])
+                ref += term
+    assert np.abs(ref).max() > 1e-3
+    assert np.abs(chi - ref).max() < 1e-6 * np.abs(ref).max()
+    # a system with every state on one side of mu does not respond
+    chi_empty = O.screening_chi0(psi, eps + 20.0, mu, t, w)
+    assert np.abs(chi_empty).max() < 1e-6 * np.abs(ref).max()
