@@ -172,7 +172,8 @@ typedef enum { BSE_PRECOND_NONE = 0, BSE_PRECOND_JACOBI = 1, BSE_PRECOND_MLP = 2
  * system per complex shift z_j = omega_j + i*Gamma_j, all n_z systems advanced
  * together (their H applications are batched; systems that have converged
  * drop out of the batch).  x_0 = 0 (or x on entry with BSE_GMRES_X0); Arnoldi by classical
- * Gram-Schmidt applied twice in FP64; Givens least squares; convergence when
+ * Gram-Schmidt in FP64, repeated for a system where its first pass removed
+ * more than half of |w|^2 (the DGKS test); Givens least squares; convergence when
  * the true residual |b - (H - z)x|/|b| <= rtol (recomputed at each restart and
  * at exit).  b [N], z [n_z] (bse_c128), x [n_z][N], iters [n_z] (H
  * applications spent on each system), rel_resid [n_z] (true residual).
