@@ -248,7 +248,10 @@ bse_status bse_jacobi_diag(bse_handle* h, double* diag);
  * indexed as in bse_setup, kshift [3] or NULL, dv the volume per grid point;
  * a [n_proj][Nk][Nb].  All complex128, host or device; FP64 arithmetic.
  * Work runs on `stream` (NULL: legacy default) and the call returns when a is
- * written.  Allocates staging copies of host arrays. */
+ * written.  Allocates staging copies of host arrays.  Returns
+ * BSE_ERR_INVALID_ARG (before any device work) for a NULL u, nk, nx, f or a,
+ * n_bands < 1, n_proj outside 1..4096, nk[d] outside 1..16, nx[d] < 1 or
+ * n_bands > Nx; BSE_ERR_OOM or BSE_ERR_CUDA from staging or the launch. */
 bse_status bse_local_projection(const bse_c128* u, const int* nk, const int* nx, int n_bands, const double* kshift,
                                 const bse_c128* f, int n_proj, double dv, bse_c128* a, void* stream);
 
@@ -262,7 +265,12 @@ bse_status bse_local_projection(const bse_c128* u, const int* nk, const int* nx,
  * [n_states] eV, chi0 [n_r][n_r]; green [n_t][n_r][n_r] receives the G_j or
  * may be NULL.  Complex128 / FP64, host or device; work on `stream` (NULL:
  * legacy default), returns when the outputs are written.  Allocates staging
- * and the G_j scratch. */
+ * and the G_j scratch.  Returns BSE_ERR_INVALID_ARG (before any device work)
+ * for a NULL psi, eps, t, w or chi0, n_r, n_states or n_t < 1, n_r > 65535 or
+ * n_t > 65535; BSE_ERR_OOM or BSE_ERR_CUDA from staging or the launches.  A
+ * node t_j = 0 with some eps[K] == mu sits on the integrand's pole and gives
+ * non-finite values: the caller's nodes must avoid it (mu between two levels,
+ * or t_j > 0). */
 bse_status bse_screening_chi0(const bse_c128* psi, const double* eps, int n_r, int n_states, double mu,
                               const double* t, const double* w, int n_t, bse_c128* green, bse_c128* chi0,
                               void* stream);

@@ -346,6 +346,7 @@ bse_status bse_screening_chi0(const bse_c128* psi, const double* eps, int n_r, i
                               const double* t, const double* w, int n_t, bse_c128* green, bse_c128* chi0,
                               void* stream) {
   if (!psi || !eps || !t || !w || !chi0 || n_r < 1 || n_states < 1 || n_t < 1) return BSE_ERR_INVALID_ARG;
+  if (n_r > 65535 || n_t > 65535) return BSE_ERR_INVALID_ARG;   // grid y and z extents of the G_j launch
   bse_handle tmp;   // error sink
   tmp.stream = (cudaStream_t)stream;
   const size_t nrr = (size_t)n_r * n_r;

@@ -63,6 +63,25 @@ def test_null_handle_calls(L):
     L.bse_destroy(None)
 
 
+def test_set_up_projection_and_screening_reject_bad_sizes_without_gpu(L):
+    from paper_1601_07728_gb300 import bse
+    buf = (ctypes.c_double * 64)()
+    nk = (ctypes.c_int * 3)(2, 2, 2)
+    nx = (ctypes.c_int * 3)(2, 2, 2)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    # 9 bands on an 8-point grid, no projectors, 17 k-points along an axis
+    assert L.bse_local_projection(p, nk, nx, 9, None, p, 1, 1.0, p, None) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_local_projection(p, nk, nx, 4, None, p, 0, 1.0, p, None) == bse.BSE_ERR_INVALID_ARG
+    nk17 = (ctypes.c_int * 3)(2, 2, 17)
+    assert L.bse_local_projection(p, nk17, nx, 4, None, p, 1, 1.0, p, None) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_local_projection(None, nk, nx, 4, None, p, 1, 1.0, p, None) == bse.BSE_ERR_INVALID_ARG
+    # more frequency nodes or grid points than one launch covers, empty sizes, missing output
+    assert L.bse_screening_chi0(p, p, 4, 4, 0.0, p, p, 70000, None, p, None) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_screening_chi0(p, p, 70000, 4, 0.0, p, p, 4, None, p, None) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_screening_chi0(p, p, 4, 0, 0.0, p, p, 4, None, p, None) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_screening_chi0(p, p, 4, 4, 0.0, p, p, 4, None, None, None) == bse.BSE_ERR_INVALID_ARG
+
+
 def test_header_cites_the_paper():
     txt = open(os.path.join(ROOT, "include", "bse.h")).read()
     for cite in ("Eq. 3", "Eq. 9", "Algorithm 1", "Eq. 14", "Eq. 2"):
