@@ -36,6 +36,15 @@ WORKLOAD_DESC = ("L2,3 edge with multiplets: 6 core states (SO split 5.7 eV), k-
                  "grid 16^3, W=-erf(r/0.5)/(5r), 36 local-basis functions, random Hermitian M (0.5 eV)")
 
 
+def workload_desc(name):
+    """Human-readable description of a workload (the generator's sizes when it is not the default one)."""
+    if name == WORKLOAD:
+        return WORKLOAD_DESC
+    from paper_1601_07728_gb300 import synth as S
+    c = S.CONFIGS.get(name, {})
+    return "%s: %s" % (name, ", ".join("%s=%s" % kv for kv in sorted(c.items()))) if c else name
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -203,7 +212,7 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "matvecs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "precision": "fp64 (NumPy/SciPy oracle)"},
+        "config": {"workload": args.workload, "desc": workload_desc(args.workload), "precision": "fp64 (NumPy/SciPy oracle)"},
         "cpu_baseline": {"value": rate, "unit": "matvecs/s", "cores": cores, "kind": "oracle",
                          "sample": "%d FP64 oracle Haydock steps of the full workload (timed steps capped at "
                                    "%.0f s of CPU time)" % (n, budget)},
@@ -469,7 +478,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max / max(steps_done, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "precision": args.precision,
+            "config": {"workload": args.workload, "desc": workload_desc(args.workload), "precision": args.precision,
                        "recursion": "f64 Haydock, no re-orthogonalisation", "n_vec": 1, "dim": n,
                        "l2": "inputs larger than L2 (u_nk 1.07 GB), no flush", "parallelism": "replicas",
                        "tiles": {"grid_to_band_split_k": tiles[0], "pipeline_stages": tiles[1],

@@ -51,3 +51,25 @@ def test_clock_summary_keeps_this_gpu_and_reasons():
 def test_workload_constants_match_the_generator():
     cfg = S.CONFIGS[bench.WORKLOAD]
     assert cfg["n_alpha"] == 6 and cfg["nk"] == (8, 8, 8) and cfg["n_bands"] == 64 and cfg["nx"] == (16, 16, 16)
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    line with the contract's keys; the small 1s workload keeps it quick."""
+    import json
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "k_edge_small",
+                                      "--steps", "3", "--warmup", "3"])
+    assert bench.main() == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "k_edge_small" and d["config"]["desc"].startswith("k_edge_small")
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
