@@ -103,7 +103,7 @@ def screening_chi0(psi, eps, mu, t, w):
 
 
 def apply_w0_loop(s, psi):
-    """W_0 psi by Algorithm 1 as printed: for each x and alpha, build phi(k),
+    """W_0 psi taking the steps of Algorithm 1 in order: for each x and alpha, build phi(k),
     transform k->R with an explicit sum, multiply by W(x, R), transform back,
     project out with e^{-ik.x} u*_nk(x).  psi is [Na][Nk][Nb].  Pure loops."""
     na, nk, nb, nx = _shape(s)
