@@ -143,3 +143,76 @@ def test_local_functions_vanish_outside_their_radius():
     r = np.linalg.norm((j - np.round(j)) * 7.4, axis=1)
     assert np.abs(f[:, r >= 2.0]).max() == 0.0
     assert np.abs(f[:, r < 2.0]).max() > 0.0
+
+
+class _OneRadialIntegral:
+    """Stands in for the generator's random stream: the `which`-th radial
+    integral drawn is (scale / n_rad) * identity, every other one is zero.
+    Draw order: F^0, F^2, then G^0 .. G^4."""
+
+    def __init__(self, which):
+        self.which, self.i = which, 0
+
+    def standard_normal(self, shape):
+        out = np.eye(shape[0]) if self.i == self.which else np.zeros(shape)
+        self.i += 1
+        return out
+
+
+_NRAD = S.LOCAL_NU * (S.LOCAL_LMAX + 1)
+_C = 0.5 / _NRAD            # the radial integral each pin turns on (scale 0.5)
+
+
+def _diag_block(M, lsel):
+    """Orbital diagonal entries [(m_c, nu, m)] of the spin-up block for local functions with l = lsel."""
+    npj = len(S.local_functions())
+    out = {}
+    for ic, mc in enumerate((-1, 0, 1)):
+        a = 2 * ic
+        for p, (nu, l, m) in enumerate(S.local_functions()):
+            if l == lsel:
+                out[(mc, nu, m)] = M[a * npj + p, a * npj + p]
+    return out
+
+
+def test_monopole_direct_term_is_a_uniform_shift():
+    """F^0 alone: <l m|C^0|l' m'> = delta, so the direct term is -F^0 times
+    the identity in every orbital and spin index (sign of the direct term)."""
+    M = S.structured_couplings(_OneRadialIntegral(0))
+    assert np.abs(M - (-_C) * np.eye(M.shape[0])).max() < 1e-14
+
+
+def test_quadrupole_direct_term_is_traceless():
+    """F^2 alone: a rank-2 tensor operator has zero trace over m, so for each
+    core m_c and radial function the diagonal of the l block sums to zero;
+    s functions do not couple at all (<0 0|C^2|0 0> = 0)."""
+    M = S.structured_couplings(_OneRadialIntegral(1))
+    assert np.abs(M).max() > 1e-3
+    for l in range(S.LOCAL_LMAX + 1):
+        d = _diag_block(M, l)
+        for mc in (-1, 0, 1):
+            for nu in range(S.LOCAL_NU):
+                tr = sum(d[(mc, nu, m)] for m in range(-l, l + 1))
+                assert abs(tr) < 1e-14, (l, mc, nu, tr)
+    for v in _diag_block(M, 0).values():
+        assert v == 0.0
+
+
+def test_dipole_exchange_closed_forms():
+    """G^1 alone (exchange through the dipole multipole, p hole): an s
+    electron sees G^1/3 on every diagonal entry, the traces over (m_c, m) of
+    the d block are 2 G^1 (sum rule 3 (2 1 1; 0 0 0)^2 = 2/5 per m), and p and
+    f electrons see nothing (parity, triangle rule)."""
+    M = S.structured_couplings(_OneRadialIntegral(3))
+    s = _diag_block(M, 0)
+    for (mc, nu, m), v in s.items():
+        assert abs(v - _C / 3) < 1e-14, (mc, nu, v)
+    d = _diag_block(M, 2)
+    for nu in range(S.LOCAL_NU):
+        tr = sum(d[(mc, nu, m)] for mc in (-1, 0, 1) for m in range(-2, 3))
+        assert abs(tr - 2 * _C) < 1e-13, (nu, tr)
+    npj = len(S.local_functions())
+    for p, (nu, l, m) in enumerate(S.local_functions()):
+        if l in (1, 3):
+            for a in range(6):
+                assert np.abs(M[a * npj + p]).max() == 0.0
