@@ -150,7 +150,8 @@ bse_status bse_haydock_batch(bse_handle* const* hs, const bse_c128* const* b, in
  *   g(z) = 1/(z - a_0 - b_1^2/(z - a_1 - ... - b_{n-1}^2/(z - a_{n-1} - t))),
  * t = 0, or (terminator != 0) the constant-chain tail continued with
  * (a_{n-1}, b_n).  a [n_vec][n_stride], bcoef [n_vec][n_stride+1],
- * steps [n_vec] (number of a_i used per vector), omega [n_omega],
+ * steps [n_vec] (number of a_i used per vector; a count above n_stride is
+ * taken as n_stride, zero or negative gives sigma = 0), omega [n_omega],
  * sigma [n_vec][n_omega].  Evaluated by a device kernel on the current
  * device's legacy default stream. */
 bse_status bse_cf_spectrum(const double* a, const double* bcoef, const int* steps, int n_vec,

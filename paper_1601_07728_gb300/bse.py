@@ -146,6 +146,35 @@ def _ptr(a):
     raise TypeError("expected numpy array or torch tensor")
 
 
+_ELEM = {"complex128": np.complex128, "float64": np.float64, "int32": np.int32}
+
+
+def _buf(a, elem, n, name):
+    """Address of a buffer the library reads or writes n elements of: checks
+    its element type and that it holds at least n elements, so that a wrong
+    array is refused here instead of being overrun."""
+    if a is None:
+        raise ValueError("%s is required" % name)
+    if isinstance(a, np.ndarray):
+        ok, size = a.dtype == _ELEM[elem], a.size
+    elif hasattr(a, "data_ptr"):
+        ok, size = str(a.dtype) == "torch." + elem, a.numel()
+    else:
+        raise TypeError("%s: expected numpy array or torch tensor" % name)
+    if not ok:
+        raise TypeError("%s must hold %s elements, not %s" % (name, elem, a.dtype))
+    if size < n:
+        raise ValueError("%s holds %d elements, %d needed" % (name, size, n))
+    return _ptr(a)
+
+
+def _n_vectors(a, dim, name):
+    """Number of N-vectors in a [N] or [V][N] array."""
+    if a.ndim not in (1, 2) or a.shape[-1] != dim:
+        raise ValueError("%s must be [%d] or [V][%d], got shape %s" % (name, dim, dim, tuple(a.shape)))
+    return 1 if a.ndim == 1 else int(a.shape[0])
+
+
 class System:
     """One absorbing site on the device (wraps a bse_handle)."""
 
@@ -211,20 +240,23 @@ class System:
 
     def apply_h(self, psi, out=None):
         """out = H psi; psi [N] or [V][N] complex128 (numpy or CUDA tensor)."""
-        nv = 1 if psi.ndim == 1 else psi.shape[0]
+        nv = _n_vectors(psi, self.dim, "psi")
         if out is None:
             out = np.empty_like(psi) if isinstance(psi, np.ndarray) else psi.new_empty(psi.shape)
-        self._check(lib().bse_apply_h(self.h, _ptr(psi), _ptr(out), nv))
+        n = nv * self.dim
+        self._check(lib().bse_apply_h(self.h, _buf(psi, "complex128", n, "psi"), _buf(out, "complex128", n, "out"),
+                                      nv))
         return out
 
     def haydock(self, b, n_steps, reorth=False, a=None, bcoef=None, steps=None):
         """Haydock coefficients (a [V][n], b [V][n+1], steps_done [V], status)."""
-        nv = 1 if b.ndim == 1 else b.shape[0]
+        nv = _n_vectors(b, self.dim, "b")
         a = np.zeros((nv, n_steps)) if a is None else a
         bcoef = np.zeros((nv, n_steps + 1)) if bcoef is None else bcoef
         steps = np.zeros(nv, dtype=np.int32) if steps is None else steps
-        st = lib().bse_haydock(self.h, _ptr(b), nv, int(n_steps), int(bool(reorth)), _ptr(a), _ptr(bcoef),
-                               _ptr(steps))
+        st = lib().bse_haydock(self.h, _buf(b, "complex128", nv * self.dim, "b"), nv, int(n_steps),
+                               int(bool(reorth)), _buf(a, "float64", nv * n_steps, "a"),
+                               _buf(bcoef, "float64", nv * (n_steps + 1), "bcoef"), _buf(steps, "int32", nv, "steps"))
         self._check(st, (BSE_OK, BSE_ERR_BREAKDOWN))
         return a, bcoef, steps, st
 
@@ -235,9 +267,9 @@ class System:
         x = np.zeros((nz, self.dim), dtype=np.complex128) if x is None else x
         iters = np.zeros(nz, dtype=np.int32)
         rel = np.zeros(nz)
-        st = lib().bse_gmres(self.h, _ptr(b), _ptr(z), nz, float(rtol), int(restart), int(max_iter),
-                             PRECOND[precond] if isinstance(precond, str) else int(precond), _ptr(x),
-                             _ptr(iters), _ptr(rel))
+        st = lib().bse_gmres(self.h, _buf(b, "complex128", self.dim, "b"), _ptr(z), nz, float(rtol), int(restart),
+                             int(max_iter), PRECOND[precond] if isinstance(precond, str) else int(precond),
+                             _buf(x, "complex128", nz * self.dim, "x"), _ptr(iters), _ptr(rel))
         self._check(st, (BSE_OK, BSE_ERR_NOT_CONVERGED))
         return x, iters, rel, st
 
@@ -325,8 +357,10 @@ class MLP:
         minimal-residual loss (steps = k >= 1) or the plain approximate-inverse loss (steps = 0)."""
         g = np.empty(self.n, dtype=np.float32)
         loss = ctypes.c_double()
-        sysg._check(lib().bse_mlp_loss_grad(sysg.h, self.h, float(omega), float(gamma), r.shape[0], _ptr(r),
-                                            int(steps), ctypes.byref(loss), g.ctypes.data))
+        nt = _n_vectors(r, sysg.dim, "r")
+        sysg._check(lib().bse_mlp_loss_grad(sysg.h, self.h, float(omega), float(gamma), nt,
+                                            _buf(r, "complex128", nt * sysg.dim, "r"), int(steps),
+                                            ctypes.byref(loss), g.ctypes.data))
         return loss.value, g
 
     def adam_step(self, grad, lr):
@@ -352,16 +386,21 @@ def haydock_batch(systems, bs, n_steps, outs=None):
     """bse_haydock_batch over Systems (each on its own stream); bs[s] [n_vec][N].
     Returns per site (a, bcoef, steps) and the per-site statuses."""
     n = len(systems)
-    n_vec = 1 if bs[0].ndim == 1 else bs[0].shape[0]
+    if len(bs) != n or (outs is not None and len(outs) != n):
+        raise ValueError("one start-vector array (and output triple) per system")
+    n_vec = _n_vectors(bs[0], systems[0].dim, "bs[0]")
+    for i in range(n):
+        if _n_vectors(bs[i], systems[i].dim, "bs[%d]" % i) != n_vec:
+            raise ValueError("every site takes the same number of start vectors")
     if outs is None:
         outs = [(np.zeros((n_vec, n_steps)), np.zeros((n_vec, n_steps + 1)), np.zeros(n_vec, dtype=np.int32))
                 for _ in range(n)]
     V = ctypes.c_void_p
     hs = (V * n)(*[s.h.value for s in systems])
-    bp = (V * n)(*[_ptr(b) for b in bs])
-    ap = (V * n)(*[_ptr(o[0]) for o in outs])
-    bcp = (V * n)(*[_ptr(o[1]) for o in outs])
-    sp = (V * n)(*[_ptr(o[2]) for o in outs])
+    bp = (V * n)(*[_buf(b, "complex128", n_vec * sy.dim, "bs") for b, sy in zip(bs, systems)])
+    ap = (V * n)(*[_buf(o[0], "float64", n_vec * n_steps, "a") for o in outs])
+    bcp = (V * n)(*[_buf(o[1], "float64", n_vec * (n_steps + 1), "bcoef") for o in outs])
+    sp = (V * n)(*[_buf(o[2], "int32", n_vec, "steps") for o in outs])
     sts = np.zeros(n, dtype=np.int32)
     st = lib().bse_haydock_batch(hs, bp, n, n_vec, int(n_steps), ap, bcp, sp, sts.ctypes.data)
     if st not in (BSE_OK, BSE_ERR_BREAKDOWN):

@@ -314,7 +314,7 @@ bse_status bse_cf_spectrum(const double* a, const double* bcoef, const int* step
   TRY(stage_in(&tmp, ss, steps, (size_t)n_vec * sizeof(int), true, "steps"));
   TRY(stage_in(&tmp, so, omega, (size_t)n_omega * sizeof(double), true, "omega"));
   TRY(stage_in(&tmp, sg, sigma, (size_t)n_vec * n_omega * sizeof(double), false, "sigma"));
-  // steps beyond n_stride are clamped by the caller contract
+  // counts in steps above n_stride are clamped by the kernel
   TRY(bse_cf_device((const double*)sa.dev, (const double*)sb.dev, (const int*)ss.dev, n_vec, n_stride,
                     (const double*)so.dev, n_omega, gamma, terminator, (double*)sg.dev, tmp.stream));
   TRY(stage_out(&tmp, sg, sigma, (size_t)n_vec * n_omega * sizeof(double), "sigma copy-out"));

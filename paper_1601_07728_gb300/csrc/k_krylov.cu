@@ -363,7 +363,7 @@ __global__ void cf_kernel(const double* __restrict__ a, const double* __restrict
   if (j >= n_omega) return;
   const double* av = a + (size_t)v * n_stride;
   const double* bv = bco + (size_t)v * (n_stride + 1);
-  const int n = steps[v];
+  const int n = min(steps[v], n_stride);   // a row holds n_stride coefficients
   if (n <= 0) {
     sigma[(size_t)v * n_omega + j] = 0.0;
     return;

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -86,3 +87,29 @@ def test_header_cites_the_paper():
     txt = open(os.path.join(ROOT, "include", "bse.h")).read()
     for cite in ("Eq. 3", "Eq. 9", "Algorithm 1", "Eq. 14", "Eq. 2"):
         assert cite in txt
+
+
+def test_binding_refuses_buffers_the_library_would_overrun():
+    """The binding checks element type and size of every array it hands to the
+    library, so a wrong array raises in Python instead of being read or
+    written past its end."""
+    from paper_1601_07728_gb300 import bse
+    v = np.zeros((2, 10), dtype=np.complex128)
+    assert bse._n_vectors(v, 10, "b") == 2 and bse._n_vectors(v[0], 10, "b") == 1
+    for bad in (np.zeros((2, 9), dtype=np.complex128), np.zeros((1, 2, 10), dtype=np.complex128)):
+        with pytest.raises(ValueError):
+            bse._n_vectors(bad, 10, "b")
+    assert bse._buf(v, "complex128", 20, "b") == v.ctypes.data
+    with pytest.raises(ValueError):
+        bse._buf(v, "complex128", 21, "b")
+    with pytest.raises(TypeError):
+        bse._buf(v.real.copy(), "complex128", 20, "b")
+    with pytest.raises(TypeError):
+        bse._buf(np.zeros(4, dtype=np.int64), "int32", 4, "steps")
+    with pytest.raises(ValueError):
+        bse._buf(None, "float64", 1, "a")
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(6, dtype=torch.float64)
+    assert bse._buf(t, "float64", 6, "a") == t.data_ptr()
+    with pytest.raises(TypeError):
+        bse._buf(t.float(), "float64", 6, "a")
