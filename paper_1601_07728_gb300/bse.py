@@ -419,17 +419,28 @@ def attach_mlp(sysg, mlp):
 
 
 def local_projection(u, nk, nx, f, dv, kshift=(0.0, 0.0, 0.0), stream=None):
-    """bse_local_projection: a [Np][Nk][Nb] = dv sum_x conj(f_p(x)) e^{ik.x} u_nk(x) (host arrays in and out)."""
-    u = np.ascontiguousarray(u, dtype=np.complex128)
-    f = np.ascontiguousarray(f, dtype=np.complex128)
+    """bse_local_projection: a [Np][Nk][Nb] = dv sum_x conj(f_p(x)) e^{ik.x} u_nk(x).
+    u [Nk][Nx][Nb] and f [Np][Nx] are numpy arrays (a is returned on the host)
+    or torch CUDA tensors (a is returned as a CUDA tensor, no staging)."""
+    device = hasattr(u, "data_ptr")
+    if not device:
+        u = np.ascontiguousarray(u, dtype=np.complex128)
+        f = np.ascontiguousarray(f, dtype=np.complex128)
     nkt, nxt, nb = u.shape
     npj = f.shape[0]
-    a = np.zeros((npj, nkt, nb), dtype=np.complex128)
+    if nkt != int(np.prod(nk)) or nxt != int(np.prod(nx)) or f.shape[-1] != nxt:
+        raise ValueError("u must be [Nk][Nx][Nb] and f [Np][Nx] for the given meshes")
+    if device:
+        import torch
+        a = torch.empty((npj, nkt, nb), dtype=torch.complex128, device=u.device)
+    else:
+        a = np.zeros((npj, nkt, nb), dtype=np.complex128)
     nk_a = (ctypes.c_int * 3)(*nk)
     nx_a = (ctypes.c_int * 3)(*nx)
     ks = (ctypes.c_double * 3)(*kshift)
-    st = lib().bse_local_projection(u.ctypes.data, nk_a, nx_a, nb, ks, f.ctypes.data, npj, float(dv), a.ctypes.data,
-                                    stream)
+    st = lib().bse_local_projection(_buf(u, "complex128", nkt * nxt * nb, "u"), nk_a, nx_a, nb, ks,
+                                    _buf(f, "complex128", npj * nxt, "f"), npj, float(dv),
+                                    _buf(a, "complex128", npj * nkt * nb, "a"), stream)
     _chk(st)
     return a
 

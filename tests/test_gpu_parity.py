@@ -136,6 +136,27 @@ def test_local_projection_matches_oracle(shape):
     assert rel(a, ref) < 1e-12
 
 
+def test_local_projection_full_size_sampled_k():
+    """Set-up projection at the size of the L2,3 workload (8^3 k, 16^3 grid,
+    64 bands, 64 local functions; u_nk 2.1 GB on the device, passed without
+    staging), sampled k-points against the oracle: the oracle's projection
+    of the single k-point m = (m1, m2, m3) is its 1-point mesh shifted by
+    m / n_k, which has the same phases e^{ik.x}."""
+    torch = pytest.importorskip("torch")
+    cfg = S.CONFIGS["l23_multiplet"]
+    nk, nx, nb = cfg["nk"], cfg["nx"], cfg["n_bands"]
+    nkt, nxt = int(np.prod(nk)), int(np.prod(nx))
+    u = S.orthonormal_bloch_device(961, nkt, nxt, nb)
+    f = S.local_functions_on_grid(nx, cfg["cell"], 2.5)
+    dv = cfg["cell"] ** 3 / nxt
+    a = bse.local_projection(u, nk, nx, torch.from_numpy(f).cuda(), dv)
+    for m in [(0, 0, 0), (0, 0, 1), (1, 2, 3), (4, 0, 7), (7, 7, 7)]:
+        k = (m[0] * nk[1] + m[1]) * nk[2] + m[2]
+        ref = O.local_projection(u[k:k + 1].cpu().numpy(), (1, 1, 1), nx, f, dv,
+                                 tuple(m[d] / nk[d] for d in range(3)))
+        assert rel(a[:, k, :].cpu().numpy(), ref[:, 0, :]) < 1e-12, m
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
 def test_structured_multiplets_match_oracle(prec):
     """The 64-function local basis (4 radial functions for each l <= 3) with
