@@ -453,3 +453,19 @@ def test_screening_chi0_equals_static_lindhard_form():
     # a system with every state on one side of mu does not respond
     chi_empty = O.screening_chi0(psi, eps + 20.0, mu, t, w)
     assert np.abs(chi_empty).max() < 1e-6 * np.abs(ref).max()
+
+
+def test_local_projection_single_k_equals_shifted_one_point_mesh():
+    """The projection at k-point m of an n_k mesh depends on k only through
+    e^{ik.x}: a one-point mesh shifted by m / n_k gives the same phases, so
+    the same coefficients (the identity the full-size GPU check samples by)."""
+    s = S.make_system_from(dict(id=960, n_alpha=1, nk=(4, 2, 3), n_bands=5, nx=(6, 4, 5), cell=7.4, eps=5.0,
+                                n_proj=0), 0)
+    f = S.local_functions_on_grid(s.nx, s.cell, 2.5)
+    dv = s.cell ** 3 / s.n_x
+    a = O.local_projection(s.u, s.nk, s.nx, f, dv)
+    for m in [(0, 0, 0), (3, 1, 2), (1, 0, 1)]:
+        k = (m[0] * s.nk[1] + m[1]) * s.nk[2] + m[2]
+        r = O.local_projection(s.u[k:k + 1], (1, 1, 1), s.nx, f, dv, tuple(m[d] / s.nk[d] for d in range(3)))
+        assert np.abs(a[:, k, :] - r[:, 0, :]).max() < 1e-14 * max(1.0, np.abs(a).max())
+    assert np.abs(a).max() > 0.1
