@@ -74,7 +74,8 @@ def _shape(s):
 
 
 # ----------------------------------------------------------------------------
-# H psi: literal Algorithm 1 (tiny inputs only)
+# set-up projection, screening, and H psi from the definitions of its terms
+# (tiny inputs only)
 # ----------------------------------------------------------------------------
 
 def local_projection(u, nk, nx, f, dv, kshift=(0.0, 0.0, 0.0)):
@@ -102,36 +103,38 @@ def screening_chi0(psi, eps, mu, t, w):
     return np.einsum("j,jrc,jcr->rc", np.asarray(w, dtype=np.float64), g, g) / TWO_PI
 
 
-def apply_w0_loop(s, psi):
-    """W_0 psi taking the steps of Algorithm 1 in order: for each x and alpha, build phi(k),
-    transform k->R with an explicit sum, multiply by W(x, R), transform back,
-    project out with e^{-ik.x} u*_nk(x).  psi is [Na][Nk][Nb].  Pure loops."""
+def bloch_on_supercell(s):
+    """Bloch functions phi_nk(x + R) = e^{i k.(x + R)} u_nk(x) / sqrt(Nk) on
+    every point x + R of the Nk-cell supercell (Sec. 3.2, Eq. 8; R indexed like
+    k), as [NR][Nx][Nk*Nb] with column (k, n), n fastest.  With orthonormal
+    u_nk columns these are orthonormal over the supercell."""
     na, nk, nb, nx = _shape(s)
-    ekx = kx_phase(s.nk, s.nx, s.kshift)
-    ekr = kr_phase(s.nk, s.kshift)
-    out = np.zeros_like(psi)
-    for x in range(nx):
-        for a in range(na):
-            phik = np.zeros(nk, dtype=np.complex128)
-            for k in range(nk):                     # phi(k) = sum_n psi e^{ikx} u_nk(x)
-                acc = 0.0j
-                for n in range(nb):
-                    acc += psi[a, k, n] * ekx[k, x] * s.u[k, x, n]
-                phik[k] = acc
-            phir = np.zeros(nk, dtype=np.complex128)
-            for r in range(nk):                     # F_{k->R}: sum_k e^{+ik.R} phi(k)
-                acc = 0.0j
-                for k in range(nk):
-                    acc += ekr[k, r] * phik[k]
-                phir[r] = acc * s.w_rx[r, x]        # times W(x, R)
-            for k in range(nk):                     # F_{R->k}: (1/Nk) sum_R e^{-ik.R} phi(R)
-                acc = 0.0j
-                for r in range(nk):
-                    acc += np.conj(ekr[k, r]) * phir[r]
-                acc /= nk
-                for n in range(nb):                 # psi' += phi(k) e^{-ikx} u*_nk(x)
-                    out[a, k, n] += acc * np.conj(ekx[k, x]) * np.conj(s.u[k, x, n])
-    return out
+    ekx = kx_phase(s.nk, s.nx, s.kshift)            # [Nk][Nx]
+    ekr = kr_phase(s.nk, s.kshift)                  # [Nk][NR]
+    phi = np.empty((nk, nx, nk * nb), dtype=np.complex128)
+    for r in range(nk):
+        for k in range(nk):
+            phase = ekr[k, r] * ekx[k, :] / np.sqrt(nk)                      # [Nx]
+            phi[r, :, k * nb:(k + 1) * nb] = phase[:, None] * s.u[k]
+    return phi
+
+
+def w0_matrix_loop(s):
+    """Matrix of the screened direct term in the Bloch basis, from its
+    definition as a local potential on the supercell (Sec. 3.2.1: W(x, R) is
+    the core-hole potential felt at the point x + R):
+        <n k|W_0|n' k'> = sum over supercell points r = x + R of
+                          conj(phi_nk(r)) W(r) phi_n'k'(r),
+    accumulated one point at a time (each point adds a rank-one term).  The
+    term does not act on the core index.  Tiny inputs only."""
+    na, nk, nb, nx = _shape(s)
+    phi = bloch_on_supercell(s)
+    wm = np.zeros((nk * nb, nk * nb), dtype=np.complex128)
+    for r in range(nk):
+        for x in range(nx):
+            f = phi[r, x]
+            wm += s.w_rx[r, x] * np.outer(np.conj(f), f)
+    return wm
 
 
 def apply_sr_loop(s, psi):
@@ -168,8 +171,10 @@ def apply_sr_loop(s, psi):
 
 
 def apply_h_loop(s, psi_flat):
-    """H psi with every term written as explicit loops (tiny inputs only).
-    H = diag(E_nk) - chi (x) I + W_0 (Algorithm 1) + V_SR."""
+    """H psi from the definitions of its terms (tiny inputs only):
+    H = diag(E_nk) - chi (x) I + W_0 + V_SR, with W_0 taken as the matrix of
+    the supercell potential between Bloch states (w0_matrix_loop) rather than
+    by the transform steps of Algorithm 1."""
     na, nk, nb, _ = _shape(s)
     psi = psi_flat.reshape(na, nk, nb)
     out = np.zeros_like(psi)
@@ -180,7 +185,9 @@ def apply_h_loop(s, psi_flat):
                 for b in range(na):
                     acc -= s.chi[a, b] * psi[b, k, n]
                 out[a, k, n] = acc
-    out += apply_w0_loop(s, psi)
+    wm = w0_matrix_loop(s)
+    for a in range(na):
+        out[a] += (wm @ psi[a].reshape(-1)).reshape(nk, nb)
     out += apply_sr_loop(s, psi)
     return out.reshape(-1)
 

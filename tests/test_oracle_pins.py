@@ -33,13 +33,27 @@ TINY = [
 # --- H psi --------------------------------------------------------------------
 
 @pytest.mark.parametrize("kw", TINY)
-def test_vectorised_equals_literal_algorithm1(kw):
-    """FFT/matmul route equals the explicit per-(x, alpha) loops of Algorithm 1."""
+def test_vectorised_equals_supercell_definition(kw):
+    """The FFT/matmul route of Algorithm 1 equals H built from the definitions
+    of its terms, with W_0 as the supercell potential's matrix between Bloch
+    states accumulated point by point (no transforms, no band sums)."""
     s = S.tiny_system(**kw)
     rng = np.random.default_rng(7)
     for _ in range(2):
         psi = S.complex_normal(rng, (s.dim,))
         assert rel(O.apply_h(s, psi), O.apply_h_loop(s, psi)) < 1e-13
+
+
+@pytest.mark.parametrize("kw", TINY)
+def test_supercell_bloch_functions_orthonormal(kw):
+    """phi_nk(x + R) = e^{ik.(x+R)} u_nk(x)/sqrt(Nk) over the supercell are
+    orthonormal (orthonormal u_nk columns and sum_R e^{i(k'-k).R} = Nk delta_kk'),
+    so W = c makes the supercell matrix c times the identity."""
+    s = S.tiny_system(**kw)
+    phi = O.bloch_on_supercell(s).reshape(-1, s.n_k * s.n_bands)
+    assert np.abs(phi.conj().T @ phi - np.eye(s.n_k * s.n_bands)).max() < 1e-13
+    s.w_rx = np.full_like(s.w_rx, -2.5)
+    assert np.abs(O.w0_matrix_loop(s) + 2.5 * np.eye(s.n_k * s.n_bands)).max() < 1e-12
 
 
 @pytest.mark.parametrize("kw", TINY)
