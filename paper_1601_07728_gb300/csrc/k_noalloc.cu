@@ -6,6 +6,7 @@
 // where an allocation's implicit synchronisation would stall other streams.
 #include "bse_internal.cuh"
 
+#include <cuda.h>
 #include <stdio.h>
 
 #include <mutex>
@@ -20,8 +21,44 @@ constexpr size_t NA_SCRATCH = (size_t)1 << 17;   // double2 entries = 2 MiB
 static __device__ __align__(256) double2 g_noalloc_scratch[NA_SCRATCH];
 
 constexpr int NA_MAX_DEV = 64;
+// device address of the array per device, and the context it was looked up
+// in: a reset device gets a new primary context, the module is loaded again
+// and the array may move, so a changed context means a fresh look-up
 double2* g_scratch_addr[NA_MAX_DEV] = {};
+CUcontext g_scratch_ctx[NA_MAX_DEV] = {};
 std::mutex g_scratch_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current_fn() {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// true if p is device memory of device `dev`
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+// byte ranges [a, a + na) and [b, b + nb) intersect
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
 
 // part[b][c][p] = sum over kn in block b of A[p][kn] psi[c][kn]
 __global__ void __launch_bounds__(256) na_partial(const double2* __restrict__ a_proj, const double2* __restrict__ psi,
@@ -111,10 +148,6 @@ extern "C" bse_status bse_short_range_noalloc(const bse_c128* a_proj, const bse_
     fprintf(stderr, "bse_short_range_noalloc: bad arguments\n");
     return BSE_ERR_INVALID_ARG;
   }
-  if ((const void*)psi == (void*)out) {
-    fprintf(stderr, "bse_short_range_noalloc: psi and out must not overlap\n");
-    return BSE_ERR_INVALID_ARG;
-  }
   const long long nc = (long long)n_vec * n_alpha;
   const long long nblk = (n_kb + NA_K - 1) / NA_K;
   const long long need = nblk * nc * n_proj + 2 * nc * n_proj;
@@ -125,21 +158,42 @@ extern "C" bse_status bse_short_range_noalloc(const bse_c128* a_proj, const bse_
             need, (long long)NA_SCRATCH, (long long)NA_SCRATCH);
     return BSE_ERR_INVALID_ARG;
   }
-  if (!bse_is_device_ptr(a_proj) || !bse_is_device_ptr(m_sr) || !bse_is_device_ptr(psi) || !bse_is_device_ptr(out)) {
-    fprintf(stderr, "bse_short_range_noalloc: every array must be device memory\n");
-    return BSE_ERR_INVALID_ARG;
-  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEV) {
     cudaGetLastError();
     return BSE_ERR_CUDA;
   }
+  if (!on_device(a_proj, dev) || !on_device(m_sr, dev) || !on_device(psi, dev) || !on_device(out, dev)) {
+    fprintf(stderr, "bse_short_range_noalloc: every array must be device memory of the current device (%d)\n", dev);
+    return BSE_ERR_INVALID_ARG;
+  }
+  // out is written while A is still read (projection out): they must not
+  // share bytes; neither may out and M.  psi is read completely before out
+  // is written (stream order), so psi and out may overlap or coincide.
+  const size_t out_bytes = (size_t)nc * n_kb * sizeof(double2);
+  if (overlaps(out, out_bytes, a_proj, (size_t)n_proj * n_kb * sizeof(double2)) ||
+      overlaps(out, out_bytes, m_sr, (size_t)n_alpha * n_proj * n_alpha * n_proj * sizeof(double2))) {
+    fprintf(stderr, "bse_short_range_noalloc: out must not overlap a_proj or m_sr\n");
+    return BSE_ERR_INVALID_ARG;
+  }
+  CtxGetCurrentFn get_ctx = ctx_get_current_fn();
+  if (!get_ctx) {
+    fprintf(stderr, "bse_short_range_noalloc: cuCtxGetCurrent unavailable\n");
+    return BSE_ERR_CUDA;
+  }
   double2* base = nullptr;
   {
-    // first call on this device: look up the device address of the static
-    // array (host code only sees a host-side stand-in for the symbol)
+    // first call on this device (or in a new context of it): look up the
+    // device address of the static array -- host code only sees a host-side
+    // stand-in for the symbol.  This is the call that loads the module, and
+    // with it the array, under lazy loading.
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    CUcontext ctx = nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) {
+      fprintf(stderr, "bse_short_range_noalloc: no current CUDA context\n");
+      return BSE_ERR_CUDA;
+    }
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
@@ -148,6 +202,7 @@ extern "C" bse_status bse_short_range_noalloc(const bse_c128* a_proj, const bse_
         return BSE_ERR_CUDA;
       }
       g_scratch_addr[dev] = (double2*)p;
+      g_scratch_ctx[dev] = ctx;
     }
     base = g_scratch_addr[dev];
   }

@@ -8,11 +8,13 @@ memory.  Here its output is compared with bse_apply_h on a system whose band
 energies, spin-orbit matrix and screened potential are zero, so that H psi is
 exactly the short-range term; both paths run in FP64, so the FP64 parity
 tolerance applies.  Two calls in a row check that the scratch left behind by
-one call does not leak into the next.  This file is collected last.
+one call does not leak into the next; the oracle's short-range term and an
+in-place call give the same result.  This file is collected last.
 """
 import numpy as np
 import pytest
 
+from oracle import bse_oracle as O
 from paper_1601_07728_gb300 import bse, synth as S
 
 pytestmark = pytest.mark.gpu
@@ -48,12 +50,44 @@ def test_noalloc_matches_apply_h_twice(kw, n_vec):
     a = torch.from_numpy(np.ascontiguousarray(s.a_proj.reshape(s.n_proj, -1))).cuda()
     m = torch.from_numpy(np.ascontiguousarray(s.m_sr)).cuda()
     stream = torch.cuda.current_stream().cuda_stream
+    # the oracle's short-range term on the same vectors (Sec. 3.2.2)
+    ref_o = O.apply_sr(s, psi.cpu().numpy().reshape(n_vec, s.n_alpha, s.n_k, s.n_bands)).reshape(n_vec, -1)
+    assert rel(ref_h, ref_o) < TOL
     for call in range(2):
         out = torch.full_like(psi, complex(7.0, -3.0))
         st = bse.short_range_noalloc(a, m, psi, out, s.n_alpha, stream=stream)
         torch.cuda.synchronize()
         assert st == bse.BSE_OK, call
-        assert rel(out.cpu().numpy(), ref_h) < TOL, call
+        got = out.cpu().numpy()
+        assert rel(got, ref_h) < TOL, call
+        assert np.abs(got - ref_o).max() <= TOL * np.abs(ref_o).max(), call
+    # in place: psi is read completely before out is written
+    work = psi.clone()
+    st = bse.short_range_noalloc(a, m, work, work, s.n_alpha, stream=stream)
+    torch.cuda.synchronize()
+    assert st == bse.BSE_OK
+    assert rel(work.cpu().numpy(), ref_h) < TOL
+
+
+def test_noalloc_rejects_out_overlapping_projectors():
+    """out is written while A is read: an output that shares bytes with a_proj
+    (or M) is refused before any work is enqueued."""
+    torch = pytest.importorskip("torch")
+    n_kb, n_proj, n_alpha = 64, 4, 1
+    a = torch.zeros((n_proj, n_kb), dtype=torch.complex128, device="cuda")
+    m = torch.zeros((n_alpha * n_proj, n_alpha * n_proj), dtype=torch.complex128, device="cuda")
+    psi = torch.zeros((1, n_kb), dtype=torch.complex128, device="cuda")
+    L = bse.lib()
+    st = L.bse_short_range_noalloc(a.data_ptr(), m.data_ptr(), psi.data_ptr(), a[1].data_ptr(), n_alpha, n_kb,
+                                   n_proj, 1, None)
+    assert st == bse.BSE_ERR_INVALID_ARG
+    st = L.bse_short_range_noalloc(a.data_ptr(), m.data_ptr(), psi.data_ptr(), m.data_ptr(), n_alpha, n_kb,
+                                   n_proj, 1, None)
+    assert st == bse.BSE_ERR_INVALID_ARG
+    host = np.zeros((1, n_kb), dtype=np.complex128)   # host memory is refused as well
+    st = L.bse_short_range_noalloc(a.data_ptr(), m.data_ptr(), psi.data_ptr(), host.ctypes.data, n_alpha, n_kb,
+                                   n_proj, 1, None)
+    assert st == bse.BSE_ERR_INVALID_ARG
 
 
 def test_noalloc_rejects_oversize():
