@@ -103,6 +103,12 @@ typedef struct {
  * them on another stream must be complete (or ordered before it) when
  * bse_setup is called.  Returns after the set-up work has finished; the
  * caller may then free or reuse its arrays.
+ * Memory budget: if the environment variable BSE_DEVICE_BYTES_LIMIT holds a
+ * decimal byte count when bse_setup is called, the sum of the device
+ * allocations bse_setup makes for the handle (its temporary staging
+ * included) may not exceed it; a set-up that would returns BSE_ERR_OOM, as it
+ * does when the device itself is out of memory.  A value that is not a
+ * decimal number gives BSE_ERR_INVALID_ARG.
  * On failure *out is NULL and nothing is leaked. */
 bse_status bse_setup(bse_handle** out, const bse_system_desc* desc);
 
@@ -277,30 +283,38 @@ bse_status bse_screening_chi0(const bse_c128* psi, const double* eps, int n_r, i
                               void* stream);
 
 /* Short-range (local direct + exchange) term alone, out = (A (x) I)^H M (A (x) I) psi,
- * computed without allocating any memory.  The paper has no counterpart: this
+ * computed without allocating memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need
  * the term -- plug-ins whose host framework owns every device byte through
  * its own pool, and real-time loops that cannot afford the synchronisation an
- * allocation implies.  No handle is used and nothing is allocated, by this library or by
- * any library it calls.
+ * allocation implies.  No handle is used.
  *   a_proj [n_proj][n_kb], m_sr [n_alpha*n_proj]^2 (index (alpha, p), alpha
  *   slow), psi and out [n_vec][n_alpha][n_kb], all complex128 DEVICE memory
- *   owned by the caller; n_kb = Nk*Nb.  Work is enqueued on `stream`
- *   (cudaStream_t, NULL = legacy default stream); the call returns without
- *   waiting for it.
+ *   of the current device, owned by the caller; n_kb = Nk*Nb.  Arrays on
+ *   another device, or host memory, give BSE_ERR_INVALID_ARG.  out may
+ *   coincide with or overlap psi (in-place use: psi is read completely before
+ *   out is written); out must not share bytes with a_proj or m_sr
+ *   (BSE_ERR_INVALID_ARG).  Work is enqueued on `stream` (cudaStream_t, NULL =
+ *   legacy default stream); the call returns without waiting for it.
  * Scratch: a 2 MiB array (131072 complex128 entries) compiled into the
- * library as a static device variable; every GPU that loads the library holds
- * it until the process exits.  The call needs
+ * library as a static device variable.  The call needs
  *   ceil(n_kb/64)*n_vec*n_alpha*n_proj + 2*n_vec*n_alpha*n_proj  entries
  * and returns BSE_ERR_INVALID_ARG (with a message on stderr) for anything
- * larger; n_proj must be in 1..64.  The first call on a device looks up the
- * array's device address with cudaGetSymbolAddress (with that device
- * current) and caches it: make that first call before any stream capture
- * begins.  Every call shares the one array and it keeps the previous call's
- * contents; each call overwrites all the entries it reads, so nothing needs
- * clearing.  Calls whose kernels overlap on the GPU (different streams, or
- * host threads using the same device) race on the scratch and must be
- * serialised by the caller. */
+ * larger; n_proj must be in 1..64.
+ * First call on a device: with CUDA's lazy module loading (the default), the
+ * first call on each device -- and the first after that device's context was
+ * reset -- loads the library's device code, and with it the 2 MiB array; that
+ * one call therefore allocates device memory (the driver's module load), and
+ * it looks up the array's device address with cudaGetSymbolAddress and caches
+ * it per device and context.  Make that first call at set-up time, before any
+ * stream capture begins; every later call allocates nothing, in this library
+ * or in any library it calls, and the array stays resident until the process
+ * exits (or the context is destroyed).
+ * Every call shares the one array and it keeps the previous call's contents;
+ * each call overwrites all the entries it reads, so nothing needs clearing.
+ * Calls whose kernels overlap on the GPU (different streams, or host threads
+ * using the same device) race on the scratch and must be serialised by the
+ * caller. */
 bse_status bse_short_range_noalloc(const bse_c128* a_proj, const bse_c128* m_sr, const bse_c128* psi,
                                    bse_c128* out, int n_alpha, int n_kb, int n_proj, int n_vec, void* stream);
 
@@ -337,6 +351,16 @@ bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* split_out, int*
  * no-op.  Synchronises the handle's stream; may reallocate the partial-sum
  * buffer. */
 bse_status bse_set_tiles(bse_handle* h, int split_k, int stages);
+
+/* Failure-detection aid, no counterpart in the paper: every wait of the
+ * tensor-core pipeline (a TMA copy landing, an MMA retiring, an accumulator
+ * being drained) gives up after `seconds` (default 2 s, range 1e-6..60).  A
+ * wait that gives up makes the kernel stop issuing work, wait for its own
+ * copies and MMAs in flight (with a fixed 2 s bound), free its tensor memory
+ * and return; the call reports BSE_ERR_TIMEOUT (its outputs are not valid)
+ * and the handle stays usable.  Other precisions have no such waits.
+ * Synchronises the handle's stream. */
+bse_status bse_set_wait_limit(bse_handle* h, double seconds);
 
 /* Measurement aid, no counterpart in the paper: when enabled, every kernel
  * launch of the handle is bracketed by CUDA events on the handle's stream

@@ -26,7 +26,7 @@ EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", 
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
            "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc",
            "bse_mlp_n_params", "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_params", "bse_mlp_outputs",
-           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0"]
+           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0", "bse_set_wait_limit"]
 KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
 
 
@@ -117,6 +117,8 @@ def lib():
     L.bse_autotune.restype = ci
     L.bse_set_tiles.argtypes = [vp, ci, ci]
     L.bse_set_tiles.restype = ci
+    L.bse_set_wait_limit.argtypes = [vp, cd]
+    L.bse_set_wait_limit.restype = ci
     L.bse_local_projection.argtypes = [vp, vp, vp, ci, vp, vp, ci, cd, vp, vp]
     L.bse_local_projection.restype = ci
     L.bse_screening_chi0.argtypes = [vp, vp, ci, ci, cd, vp, vp, ci, vp, vp, vp]
@@ -282,6 +284,10 @@ class System:
     def set_tiles(self, split_k=0, stages=0):
         """Fix the tensor-core tile parameters (0 = the set-up rule)."""
         self._check(lib().bse_set_tiles(self.h, int(split_k), int(stages)))
+
+    def set_wait_limit(self, seconds):
+        """Limit of every wait of the tensor-core pipeline (BSE_ERR_TIMEOUT beyond it)."""
+        self._check(lib().bse_set_wait_limit(self.h, float(seconds)))
 
     def profile(self, enable=True):
         """Turn per-launch CUDA-event timing on (resets totals) or off."""

@@ -3,6 +3,7 @@
 #include "bse_internal.cuh"
 
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -22,6 +23,20 @@ bool bse_is_device_ptr(const void* p) {
 bse_status bse_fail(bse_handle* h, bse_status s, const std::string& msg) {
   if (h && s != BSE_OK) h->err = msg;
   return s;
+}
+
+bse_status bse_handle_malloc(bse_handle* h, void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (h->dev_cap && h->dev_bytes + bytes > h->dev_cap)
+    return bse_fail(h, BSE_ERR_OOM, std::string("device memory cap reached allocating ") + what);
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return bse_fail(h, BSE_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+  }
+  h->dev_bytes += bytes;
+  return BSE_OK;
 }
 
 bse_status bse_cuda_check(bse_handle* h, cudaError_t e, const char* what) {
@@ -179,6 +194,12 @@ bse_status bse_setup(bse_handle** out, const bse_system_desc* d) {
   if (h->nb > h->nx) return bad("n_bands must not exceed the grid size Nx");
   h->N = (long long)h->na * h->nk * h->nb;
   h->stream = (cudaStream_t)d->stream;
+  if (const char* cap = getenv("BSE_DEVICE_BYTES_LIMIT")) {
+    char* end = nullptr;
+    const unsigned long long v = strtoull(cap, &end, 10);
+    if (end == cap || *end != '\0') return bad("BSE_DEVICE_BYTES_LIMIT must be a decimal byte count");
+    h->dev_cap = (size_t)v;
+  }
   if (h->prec == BSE_PREC_SPLIT_BF16) {
     if ((long long)h->max_vec * h->na * 2 > 256) return bad("split-bf16 form needs 2*max_vec*n_alpha <= 256");
   }

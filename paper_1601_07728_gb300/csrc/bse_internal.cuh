@@ -109,9 +109,21 @@ struct bse_handle {
   long long prof_count[BSE_K_COUNT] = {0};
   double prof_ms[BSE_K_COUNT] = {0};
 
+  // limit of each wait of the tensor-core pipeline (bse_set_wait_limit)
+  unsigned long long tc_wait_ns = 2000000000ull;
+
+  // device memory allocated for the handle by bse_setup, and the cap on it
+  // (BSE_DEVICE_BYTES_LIMIT in the environment at set-up; 0 = none)
+  size_t dev_bytes = 0;
+  size_t dev_cap = 0;
+
   long long launches = 0;
   std::string err;
 };
+
+// cudaMalloc for a handle's set-up buffers, counted against h->dev_cap
+// (BSE_ERR_OOM beyond it, or when the device is out of memory)
+bse_status bse_handle_malloc(bse_handle* h, void** p, size_t bytes, const char* what);
 
 // bracket a launch with profiling events (no-op unless enabled)
 void bse_prof_begin(bse_handle* h, int kind);

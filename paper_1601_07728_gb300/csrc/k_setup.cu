@@ -142,13 +142,10 @@ __global__ void diag_total_kernel(const double* __restrict__ e, const double2* _
 
 template <typename T>
 bse_status dev_alloc(bse_handle* h, T** p, size_t bytes, const char* what) {
-  cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    return bse_fail(h, BSE_ERR_OOM, std::string("cudaMalloc failed for ") + what);
-  }
-  return BSE_OK;
+  void* q = nullptr;
+  const bse_status s = bse_handle_malloc(h, &q, bytes, what);
+  *p = (T*)q;
+  return s;
 }
 
 #define TRY(x)                          \

@@ -59,14 +59,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of the given parity; false on timeout or abort.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait (limit_ns of %globaltimer) for the phase of the given parity;
+// false on timeout or abort.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, unsigned long long limit_ns) {
   if (mbar_try(a, parity)) return true;
   const unsigned long long t0 = gtime();
   while (true) {
     if (mbar_try(a, parity)) return true;
     if (*abort_flag) return false;
-    if (gtime() - t0 > WAIT_NS) return false;
+    if (gtime() - t0 > limit_ns) return false;
   }
 }
 
@@ -157,6 +158,7 @@ struct TcParams {
   float2* out;
   int nk, nx, nb, nc;
   int* err;
+  unsigned long long wait_ns;   // limit of each pipeline wait (the drain after an abort keeps WAIT_NS)
 };
 
 struct Tile {
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kb = 0; kb < tl.nkb; ++kb, ++it) {
         const int s = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, p.wait_ns)) {
           ok = false;
           break;
         }
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       Tile tl = decode(p, t);
       const int acc = local & 1;
       const uint32_t aph = (uint32_t)(local >> 1) & 1u;
-      if (!mbar_wait(tempty(acc), aph ^ 1u, abort_flag)) {
+      if (!mbar_wait(tempty(acc), aph ^ 1u, abort_flag, p.wait_ns)) {
         ok = false;
         break;
       }
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kb = 0; kb < tl.nkb; ++kb, ++it) {
         const int s = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (!mbar_wait(full(s), ph, abort_flag)) {
+        if (!mbar_wait(full(s), ph, abort_flag, p.wait_ns)) {
           ok = false;
           break;
         }
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     // all issued MMAs retire before the teardown frees TMEM
     mma_commit(fin);
-    if (!mbar_wait(fin, 0, abort_flag)) {
+    if (!mbar_wait(fin, 0, abort_flag, WAIT_NS)) {
       // abort raised elsewhere: still give the last MMAs a bounded grace period
       const unsigned long long t0 = gtime();
       while (!mbar_try(fin, 0) && gtime() - t0 < WAIT_NS) {
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       Tile tl = decode(p, t);
       const int acc = local & 1;
       const uint32_t aph = (uint32_t)(local >> 1) & 1u;
-      if (!mbar_wait(tfull(acc), aph, abort_flag)) {
+      if (!mbar_wait(tfull(acc), aph, abort_flag, p.wait_ns)) {
         if (lane == 0) {
           atomicExch(p.err, 1);
           *abort_flag = 1;
@@ -797,6 +799,7 @@ bse_status launch_gemm(bse_handle* h, TcState* ts, int mode, const CUtensorMap& 
   while (cols < (uint32_t)(2 * p.nn)) cols <<= 1;
   p.tmem_cols = cols;
   p.err = ts->err;
+  p.wait_ns = h->tc_wait_ns;
   const size_t smem = 1024 + (size_t)p.stages * (2 * TC_M * 128 + 2 * p.nn * 128) + 256;
   cudaFuncSetAttribute(tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = p.ntiles < ts->sms ? p.ntiles : ts->sms;
@@ -826,14 +829,17 @@ bse_status bse_tc_prepare(bse_handle* h) {
   const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
   const size_t x64 = (size_t)(h->nx + TC_KB - 1) / TC_KB;
   const size_t nbf = (size_t)h->nk * x64 * ts->nnmax * TC_KB;   // K-tiled [k][x/64][row][64]
-  if (cudaMalloc((void**)&h->bpsi, 2 * nbp * sizeof(__nv_bfloat16)) != cudaSuccess ||
-      cudaMalloc((void**)&h->psi_f, (size_t)h->max_vec * h->na * h->nk * h->nb * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc((void**)&h->bphi, 2 * nbf * sizeof(__nv_bfloat16)) != cudaSuccess ||
-      cudaMalloc((void**)&h->part, (size_t)ts->smax * h->nk * h->nb * h->na * h->max_vec * sizeof(float2)) !=
-          cudaSuccess ||
-      cudaMalloc((void**)&h->tmap, 256) != cudaSuccess) {
-    cudaGetLastError();
-    return bse_fail(h, BSE_ERR_OOM, "tensor-core scratch");
+  {
+    bse_status s = bse_handle_malloc(h, (void**)&h->bpsi, 2 * nbp * sizeof(__nv_bfloat16), "band->grid operand");
+    if (s == BSE_OK)
+      s = bse_handle_malloc(h, (void**)&h->psi_f, (size_t)h->max_vec * h->na * h->nk * h->nb * sizeof(float2),
+                            "FP32 psi");
+    if (s == BSE_OK) s = bse_handle_malloc(h, (void**)&h->bphi, 2 * nbf * sizeof(__nv_bfloat16), "grid->band operand");
+    if (s == BSE_OK)
+      s = bse_handle_malloc(h, (void**)&h->part,
+                            (size_t)ts->smax * h->nk * h->nb * h->na * h->max_vec * sizeof(float2), "split-K partials");
+    if (s == BSE_OK) s = bse_handle_malloc(h, (void**)&h->tmap, 256, "tensor-core error word");
+    if (s != BSE_OK) return s;
   }
   ts->err = (int*)h->tmap;
   cudaMemsetAsync(ts->err, 0, 256, h->stream);
@@ -988,6 +994,17 @@ int bse_tc_final_blocks(const bse_handle* h) {
   return (int)bk;
 }
 
+// Limit of every pipeline wait of the tensor-core kernel (see bse_set_wait_limit in bse.h).
+extern "C" bse_status bse_set_wait_limit(bse_handle* h, double seconds) {
+  if (!h) return BSE_ERR_INVALID_ARG;
+  if (!(seconds >= 1e-6 && seconds <= 60.0))
+    return bse_fail(h, BSE_ERR_INVALID_ARG, "set_wait_limit: need 1e-6 <= seconds <= 60");
+  const bse_status ss = bse_cuda_check(h, cudaStreamSynchronize(h->stream), "set_wait_limit sync");
+  if (ss != BSE_OK) return ss;
+  h->tc_wait_ns = (unsigned long long)(seconds * 1e9);
+  return BSE_OK;
+}
+
 // Fixed tile parameters (see bse_set_tiles in bse.h).
 extern "C" bse_status bse_set_tiles(bse_handle* h, int split_k, int stages) {
   if (!h) return BSE_ERR_INVALID_ARG;
@@ -1117,6 +1134,10 @@ bse_status bse_tc_status(bse_handle* h) {
   int e = 0;
   if (cudaMemcpy(&e, ts->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return bse_cuda_check(h, cudaGetLastError(), "tc status");
-  if (e) return bse_fail(h, BSE_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+  if (e) {
+    // reported once: clear the word so that later calls on the handle start clean
+    if (cudaMemset(ts->err, 0, sizeof(int)) != cudaSuccess) return bse_cuda_check(h, cudaGetLastError(), "tc status reset");
+    return bse_fail(h, BSE_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+  }
   return BSE_OK;
 }

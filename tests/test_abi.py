@@ -58,6 +58,7 @@ def test_null_handle_calls(L):
     assert L.bse_last_error(None) == b"null handle"
     assert L.bse_autotune(None, 1, 1, None, None) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_set_tiles(None, 2, 4) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_set_wait_limit(None, 1.0) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_haydock(None, None, 1, 1, 0, None, None, None) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_gmres(None, None, None, 1, 1e-6, 30, 100, 0, None, None, None) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_mlp_train(None, None, 1, None, 1, 1, 1, 1e-3, 0, 10, None, None) == bse.BSE_ERR_INVALID_ARG
@@ -113,3 +114,19 @@ def test_binding_refuses_buffers_the_library_would_overrun():
     assert bse._buf(t, "float64", 6, "a") == t.data_ptr()
     with pytest.raises(TypeError):
         bse._buf(t.float(), "float64", 6, "a")
+
+
+def test_device_bytes_limit_must_be_a_number(L, monkeypatch):
+    """A malformed BSE_DEVICE_BYTES_LIMIT is refused before any device work."""
+    from paper_1601_07728_gb300 import bse
+    d = bse.Desc()
+    d.n_alpha = 1
+    d.nk = (ctypes.c_int * 3)(1, 1, 1)
+    d.n_bands = 1
+    d.nx = (ctypes.c_int * 3)(1, 1, 2)
+    dummy = np.zeros(8, dtype=np.complex128)
+    d.u = d.e_nk = d.chi = d.w_rx = dummy.ctypes.data
+    h = ctypes.c_void_p()
+    monkeypatch.setenv("BSE_DEVICE_BYTES_LIMIT", "lots")
+    assert L.bse_setup(ctypes.byref(h), ctypes.byref(d)) == bse.BSE_ERR_INVALID_ARG
+    assert not h.value
