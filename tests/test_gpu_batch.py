@@ -5,6 +5,7 @@ import pytest
 
 from oracle import bse_oracle as O
 from paper_1601_07728_gb300 import bse, synth as S
+from parity_check import close
 
 pytestmark = pytest.mark.gpu
 
@@ -29,11 +30,11 @@ def test_batch_matches_single_and_oracle(prec):
         bs.append(S.make_start_vectors(s, 1, seed=kw["seed"]))
     outs, sts = bse.haydock_batch(gpus, bs, 30)
     assert np.all(sts == bse.BSE_OK)
-    tol = 1e-9 if prec == "fp64" else 1e-4
-    for s, g, b, (a, bc, st) in zip(systems, gpus, bs, outs):
+    tol = (1e-9, 1e-9) if prec == "fp64" else (2e-5, 5e-5)
+    for i, (s, g, b, (a, bc, st)) in enumerate(zip(systems, gpus, bs, outs)):
         assert st[0] == 30
         a1, bc1, _, _ = g.haydock(b, 30)
         assert np.array_equal(a, a1) and np.array_equal(bc, bc1)   # same kernels, fixed-order sums
         ao, bo, _, _ = O.haydock(lambda v: O.apply_h(s, v), b[0], 30)
-        assert np.allclose(a[0][:20], ao[:20], rtol=tol, atol=tol * 10)
-        assert np.allclose(bc[0][:21], bo[:21], rtol=tol, atol=tol * 10)
+        close("batch/a20/%s/site%d" % (prec, i), a[0][:20], ao[:20], tol)
+        close("batch/b21/%s/site%d" % (prec, i), bc[0][:21], bo[:21], tol)

@@ -4,7 +4,11 @@ epsilon 6 (Sec. 4 scaling study; N = 49,152).
 
 * H psi of the FP64 and split-bf16 forms against the FP64 oracle matvec on
   the three start vectors (the oracle's per-k matmul + FFT form, exact up to
-  rounding order): 1e-11 and 1e-4 relative, as for the smaller workloads.
+  rounding order), in relative L2 and per element, as for the smaller
+  workloads.
+* A 20-step Haydock prefix of the three polarisations batched in the
+  split-bf16 form against the oracle's own 20-step run of the first one:
+  coefficients and the 20-step spectrum.
 * 300 Haydock steps of the three polarisations batched in the split-bf16 form
   (GEMM N-dimension 18): the spectrum of the first is within 1e-4 relative L2
   of the spectrum the plain FP64 GPU form gives for the same start vector
@@ -18,6 +22,7 @@ import pytest
 
 from oracle import bse_oracle as O
 from paper_1601_07728_gb300 import bse, synth as S
+from parity_check import close
 
 pytestmark = pytest.mark.gpu
 
@@ -33,14 +38,40 @@ def sc():
     return s, b, O.apply_h(s, b)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("split_bf16", 1e-4)])
-def test_supercell_matvec_matches_oracle(sc, prec, tol):
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_supercell_matvec_matches_oracle(sc, prec):
     s, b, ref = sc
     sysg = bse.System(s, precision=prec, max_vec=3)
     out = sysg.apply_h(b)
     sysg.close()
     for v in range(3):
-        assert rel(out[v], ref[v]) < tol
+        close("supercell/apply_h/%s/v%d" % (prec, v), out[v], ref[v], prec)
+
+
+def test_supercell_haydock_prefix_matches_oracle(sc):
+    """20 Haydock steps: GPU split-bf16 (three polarisations batched) against
+    the oracle's 20-step run of the first start vector."""
+    s, b, ref = sc
+    mixed = bse.System(s, precision="split_bf16", max_vec=3)
+    a, bc, steps, st = mixed.haydock(b, 20)
+    mixed.close()
+    assert st == bse.BSE_OK and list(steps) == [20, 20, 20]
+    first = {"v": True}
+
+    def apply(v):
+        # the fixture already holds H b_0 (step 0 applies H to b_0 / |b_0|)
+        if first["v"]:
+            first["v"] = False
+            return ref[0] / np.linalg.norm(b[0])
+        return O.apply_h(s, v)
+
+    ao, bo, nd, _ = O.haydock(apply, b[0], 20)
+    assert nd == 20
+    close("supercell/prefix20_a/split_bf16", a[0], ao, (2e-5, 5e-5))
+    close("supercell/prefix20_b/split_bf16", bc[0], bo, (2e-5, 5e-5))
+    om = S.omega_grid()
+    close("supercell/prefix20_spectrum/split_bf16", bse.cf_spectrum(a, bc, steps, om, 0.5)[0],
+          O.cf_spectrum(ao, bo, om, 0.5), (1e-4, 1e-4))
 
 
 def test_supercell_300_step_spectra_batched_vs_fp64(sc):
@@ -56,4 +87,4 @@ def test_supercell_300_step_spectra_batched_vs_fp64(sc):
     plain.close()
     assert st64 == bse.BSE_OK and s64[0] == 300
     sig64 = bse.cf_spectrum(a64, b64, s64, om, 0.5)[0]
-    assert rel(sig[0], sig64) < 1e-4
+    close("supercell/spectrum300_vs_fp64_form", sig[0], sig64, (1e-4, 1e-4))
