@@ -66,6 +66,12 @@ def parse():
                    help="shifts (every n-th of the GMRES set) also solved by the plain FP64 form (0 = skip)")
     p.add_argument("--train-omega", type=int, default=8, help="training shifts of the learned preconditioner")
     p.add_argument("--train-epochs", type=int, default=10)
+    p.add_argument("--fp64-steps", type=int, default=10,
+                   help="captured Haydock steps of the plain FP64 form on the same workload (0 = skip)")
+    p.add_argument("--supercell-steps", type=int, default=20,
+                   help="timed Haydock steps on the 48^3-grid supercell workload (0 = skip)")
+    p.add_argument("--sites", type=int, default=8,
+                   help="sites of the many-site workload run in one batched launch of 200 steps (0 = skip)")
     return p.parse_args()
 
 
@@ -172,6 +178,35 @@ def algorithmic_bytes(s, prec, n_vec=1):
         out["kconv"] = phi + nk * nx * nc * 8 + w
         out["grid_to_band"] = u + nk * nx * nc * 8 + 2 * vec + npj * nk * nb * 16 + nk * nb * 8
     return out
+
+
+def u_bytes(s, prec="split_bf16"):
+    """Bytes of one streamed copy of u_nk (complex64-equivalent for the reduced forms)."""
+    return s.n_k * s.n_x * s.n_bands * (16 if prec == "fp64" else 8)
+
+
+def matvec_flops(s):
+    """Real flops of the two band<->grid contractions of one H psi (8 per complex MAC each)."""
+    return 2 * 8 * s.n_k * s.n_x * s.n_bands * s.n_alpha
+
+
+def timed_haydock(sysg, db, steps, stream, warmup=2):
+    """Device time (ms) of one captured Haydock run of `steps` steps after a short warm-up."""
+    import torch
+    nv = 1 if db.ndim == 1 else db.shape[0]
+    a = torch.zeros((nv, steps), dtype=torch.float64, device="cuda")
+    bb = torch.zeros((nv, steps + 1), dtype=torch.float64, device="cuda")
+    st = torch.zeros(nv, dtype=torch.int32, device="cuda")
+    w = max(1, warmup)
+    sysg.haydock(db, w, a=a[:, :w].contiguous(), bcoef=bb[:, :w + 1].contiguous(), steps=st)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sysg.haydock(db, steps, a=a, bcoef=bb, steps=st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), int(st.sum().item()), a, bb, st
 
 
 def cpu_oracle_rate(s, b, seconds, max_steps=None):
@@ -318,19 +353,37 @@ def main():
     steps_done = int(st_d.item())
     value = job_rate(steps_done, t_max / 1e3, world)
 
-    # spectrum error of this run against the FP64 oracle's stored Haydock
-    # coefficients for the same workload and start vector (both spectra
-    # evaluated by the same continued fraction on the 2000-point grid)
+    # spectrum error against the FP64 oracle's stored 200-step Haydock run of
+    # the same workload and start vector (tests/golden, written by the oracle
+    # only): a separate 200-step run of this form, whatever --steps is, both
+    # spectra evaluated by the same continued fraction on the 2000-point grid
     spec = None
+    om = np.linspace(-5.0, 30.0, 2000)
     gold = os.path.join(ROOT, "tests", "golden", "%s_haydock200.npz" % args.workload)
-    if os.path.exists(gold) and steps_done > 0:
+    if os.path.exists(gold):
         g = np.load(gold)
-        kk = min(steps_done, int(g["steps"]))
-        om = np.linspace(-5.0, 30.0, 2000)
-        sg = bse.cf_spectrum(a_d.cpu().numpy()[:kk], b_d.cpu().numpy()[:kk + 1], kk, om, 0.5)[0]
+        kk = int(g["steps"])
+        a200, b200, st200 = sysg.haydock(b, kk)[:3]
+        sg = bse.cf_spectrum(a200, b200, st200, om, 0.5)[0]
         so = bse.cf_spectrum(g["a"][:kk], g["b"][:kk + 1], kk, om, 0.5)[0]
-        spec = {"steps": kk, "rel_l2_vs_fp64_oracle": float(np.linalg.norm(sg - so) / np.linalg.norm(so)),
-                "grid": "2000 omega in [-5, 30] eV, Gamma 0.5 eV"}
+        spec = {"steps": int(st200[0]), "rel_l2_vs_fp64_oracle": float(np.linalg.norm(sg - so) / np.linalg.norm(so)),
+                "max_rel_vs_fp64_oracle": float(np.abs(sg - so).max() / np.abs(so).max()),
+                "grid": "2000 omega in [-5, 30] eV, Gamma 0.5 eV",
+                "reference": "stored FP64 oracle Haydock run (tests/golden/%s_haydock200.npz)" % args.workload}
+
+    # the plain FP64 form on the same workload: a few captured steps
+    fp64_form = None
+    if args.fp64_steps > 0:
+        sys64 = bse.System(s, precision="fp64", max_vec=1, stream=stream.cuda_stream)
+        ms64, done64, _, _, _ = timed_haydock(sys64, db, args.fp64_steps, stream)
+        sys64.close()
+        ms64 = max_over_ranks(ms64, dist)
+        fl = matvec_flops(s)
+        fp64_form = {"matvecs_per_s": job_rate(done64, ms64 / 1e3, world), "ms_per_step": ms64 / args.fp64_steps,
+                     "steps": args.fp64_steps, "gflop_per_matvec": fl / 1e9,
+                     "tflops": fl * done64 / (ms64 / 1e3) / 1e12, "fp64_peak_tflops_nominal": 1.25,
+                     "frac_of_nominal_fp64": fl * done64 / (ms64 / 1e3) / 1e12 / 1.25,
+                     "speedup_of_headline": value / job_rate(done64, ms64 / 1e3, world)}
 
     # three polarisations (start vectors) advanced together: one pass over u_nk
     # per step serves all three H psi (GEMM columns 3 x 6); the first vector is
@@ -360,9 +413,11 @@ def main():
         pol = {"n_vec": npol, "matvecs_per_s": job_rate(done3, pms / 1e3, world), "ms_per_step": pms / K,
                "note": "polarisations batched as GEMM columns; u_nk read once per step for all of them"}
         if spec is not None:
-            kk = spec["steps"]
-            s0 = bse.cf_spectrum(a3[0].cpu().numpy()[:kk], bb3[0].cpu().numpy()[:kk + 1], kk, om, 0.5)[0]
-            pol["rel_l2_vs_fp64_oracle_vector0"] = float(np.linalg.norm(s0 - so) / np.linalg.norm(so))
+            k3 = min(K, int(g["steps"]))
+            s0 = bse.cf_spectrum(a3[0].cpu().numpy()[:k3], bb3[0].cpu().numpy()[:k3 + 1], k3, om, 0.5)[0]
+            r0 = bse.cf_spectrum(g["a"][:k3], g["b"][:k3 + 1], k3, om, 0.5)[0]
+            pol["spectrum_steps"] = k3
+            pol["rel_l2_vs_fp64_oracle_vector0"] = float(np.linalg.norm(s0 - r0) / np.linalg.norm(r0))
         sys3.close()
         del b3
 
@@ -434,6 +489,82 @@ def main():
         sys_g.close()
         del xg
 
+    peak, peak_kind = peaks()
+
+    # the 48^3-grid supercell workload (6 core states, 2^3 k, 1024 bands, 36
+    # local functions; u_nk 14.5 GB complex128 drawn on the device): captured
+    # Haydock steps of one start vector and of three polarisations batched
+    sc = None
+    if args.supercell_steps > 0:
+        import torch as _t
+        cfg4 = S.CONFIGS["supercell_48"]
+        s4 = S.make_system_device(cfg4, name="supercell_48")
+        b4 = S.make_start_vectors(s4, 3)
+        sc = {"workload": "supercell_48", "desc": workload_desc("supercell_48"), "steps": args.supercell_steps}
+        for nv in (1, 3):
+            g4 = bse.System(s4, precision=args.precision, max_vec=nv, stream=stream.cuda_stream)
+            tiles4 = g4.autotune(n_vec=nv, reps=3)
+            db4 = _t.from_numpy(b4[:nv] if nv > 1 else b4[0]).to("cuda")
+            ms4, done4, _, _, _ = timed_haydock(g4, db4, args.supercell_steps, stream)
+            g4.close()
+            ms4 = max_over_ranks(ms4, dist)
+            per_step = ms4 / args.supercell_steps / 1e3
+            ub = u_bytes(s4, args.precision)
+            leg4 = {"matvecs_per_s": job_rate(done4, ms4 / 1e3, world), "ms_per_step": per_step * 1e3,
+                    "spectra_per_s_300_steps": job_rate(nv, per_step * 300, world),
+                    "tiles": {"grid_to_band_split_k": tiles4[0], "pipeline_stages": tiles4[1]},
+                    "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+                                 "alg_bytes_per_step": 2 * ub, "achieved": 2 * ub / per_step / 1e9,
+                                 "frac": 2 * ub / per_step / 1e9 / peak,
+                                 "note": "two streams of u_nk per step (band->grid, grid->band)"}}
+            sc["n_vec_%d" % nv] = leg4
+            del db4
+        del s4
+        _t.cuda.empty_cache()
+
+    # many absorbing sites of uneven size (k mesh n^3, n = 4..8; grid m^3,
+    # m = 12..20; 32..256 bands; 1 or 6 core states): the first --sites sites
+    # of the seeded 64-site set, one graph-captured launch of 200 Haydock steps
+    sites = None
+    if args.sites > 0:
+        import torch as _t
+        n_s = args.sites
+        systems, bsl, tot_u, tot_mv = [], [], 0, 0
+        for i in range(n_s):
+            cfg = S.batched_site_config(i)
+            si = S.make_system_device(cfg, site=i, name="sites64")
+            gi = bse.System(si, precision=args.precision, stream=_t.cuda.Stream().cuda_stream)
+            gi.autotune(n_vec=1, reps=3)
+            systems.append(gi)
+            bsl.append(_t.from_numpy(S.make_start_vectors(si, 1, seed=i)).to("cuda"))
+            tot_u += u_bytes(si, args.precision)
+            del si
+            _t.cuda.empty_cache()
+        outs = [(_t.zeros((1, 200), dtype=_t.float64, device="cuda"), _t.zeros((1, 201), dtype=_t.float64, device="cuda"),
+                 _t.zeros(1, dtype=_t.int32, device="cuda")) for _ in range(n_s)]
+        bse.haydock_batch(systems, bsl, 3, outs=[(o[0][:, :3].contiguous(), o[1][:, :4].contiguous(), o[2])
+                                                 for o in outs])   # warm-up
+        _t.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        _, sts = bse.haydock_batch(systems, bsl, 200, outs=outs)
+        _t.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, dist)
+        done_s = int(sum(int(o[2].sum().item()) for o in outs))
+        for gi in systems:
+            gi.close()
+        del systems, bsl, outs
+        _t.cuda.empty_cache()
+        sites = {"n_sites": n_s, "steps": 200, "seconds": el, "spectra_per_s": job_rate(n_s, el, world),
+                 "matvecs_per_s": job_rate(done_s, el, world), "statuses_ok": bool(np.all(sts == 0)),
+                 "u_bytes_total": tot_u,
+                 "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+                              "alg_bytes_per_batched_step": 2 * tot_u,
+                              "achieved": 2 * tot_u * 200 / el / 1e9, "frac": 2 * tot_u * 200 / el / 1e9 / peak,
+                              "note": "wall time of the one bse_haydock_batch call (graph capture and launch "
+                                      "included); two streams of every site's u_nk per batched step"},
+                 "sites": "batched_site_config(0..%d): uneven k meshes, grids, bands and core states" % (n_s - 1)}
+
     # end to end: the public call with pinned host buffers, H2D + D2H every step
     hp = torch.from_numpy(b).pin_memory()
     ho = torch.empty_like(hp).pin_memory()
@@ -451,7 +582,6 @@ def main():
     e2e = job_rate(k_e2e, el, world)
 
     # roofline of the dominant kernel class
-    peak, peak_kind = peaks()
     dom = max(("band_to_grid", "kconv", "grid_to_band"), key=lambda k: prof[k][1])
     nl, tot = prof[dom]
     alg = algorithmic_bytes(s, args.precision)[dom]
@@ -492,7 +622,10 @@ def main():
                     "api": "bse_apply_h with pinned host psi/hpsi"},
             "gpu_launches": launches,
             "spectrum": spec,
+            "fp64_form": fp64_form,
             "polarisations": pol,
+            "supercell": sc,
+            "sites": sites,
             "gmres": gm,
             "clocks": clocks,
             "cpu_baseline": cpu,

@@ -73,3 +73,11 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+
+
+def test_step_bytes_and_flops_of_the_l23_workload():
+    """Two streams of u_nk per step bound the HBM roofline; the FP64 form's
+    flops are the two complex contractions (8 real flops per complex MAC)."""
+    assert bench.u_bytes(_Shape) == 512 * 4096 * 64 * 8
+    assert bench.u_bytes(_Shape, "fp64") == 512 * 4096 * 64 * 16
+    assert bench.matvec_flops(_Shape) == 2 * 8 * 512 * 4096 * 64 * 6
