@@ -427,6 +427,46 @@ def structured_system(cfg: dict, site: int = 0, name: str = "structured") -> BSE
     return s
 
 
+STREAM_VAL = 7   # valence final state of the RIXS two-step
+
+
+def valence_final_state(core: BSESystem, n_v: int = 10, seed: int = 0, w_scale: float = 0.5,
+                        m_scale: float = 0.3, e_range=(2.0, 8.0)):
+    """Final-state system of the RIXS two-step and its emission operator.
+
+    The final state of resonant inelastic scattering has the core hole filled
+    from the valence band: a valence hole v (one of n_v localised valence
+    states, e.g. the 10 spin-orbitals of a 3d shell) with the photo-electron
+    (n, k) left where the absorption put it.  Its Hamiltonian is taken of the
+    same form as the core-hole one, with the hole index running over v:
+    band energies E_nk, the hole term -chi_val with chi_val = -diag(eps_v) +
+    a Hermitian hopping (hole binding energies eps_v ~ U[e_range] eV, so that
+    energy losses are E_nk + eps_v), the long-range direct term with W scaled
+    by w_scale (a valence hole is screened more and less localised than a
+    core hole), and the short-range term through the same local functions
+    with seeded Hermitian couplings of scale m_scale eV.  The emission
+    operator D [n_v][n_alpha] (dipole matrix elements between the valence
+    and core orbitals) is seeded complex normal with unit Frobenius norm per
+    row.  Returns (final-state BSESystem, D)."""
+    cid = int(core.meta.get("id", 99))
+    rng = rng_for(cid, 5000 + seed, STREAM_VAL)
+    eps_v = rng.uniform(e_range[0], e_range[1], size=n_v)
+    hop = random_hermitian(rng, n_v, 0.25)
+    chi = -np.diag(eps_v).astype(np.complex128) + hop
+    a_proj = core.a_proj
+    m_sr = None
+    if a_proj is not None:
+        m_sr = random_hermitian(rng, n_v * a_proj.shape[0], m_scale)
+    d = complex_normal(rng, (n_v, core.n_alpha))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    meta = dict(core.meta)
+    meta["id"] = cid + 500
+    val = BSESystem(n_alpha=n_v, nk=core.nk, n_bands=core.n_bands, nx=core.nx, cell=core.cell, eps=core.eps,
+                    u=core.u, e_nk=core.e_nk, chi=chi, w_rx=core.w_rx * w_scale, a_proj=a_proj, m_sr=m_sr,
+                    kshift=core.kshift, name=core.name + "_valence", meta=meta)
+    return val, d
+
+
 def batched_site_config(site: int) -> dict:
     """Shape of one site of the many-site workload: k mesh n^3 with
     n ~ U{4..8}, grid m^3 with m ~ U{12..20}, Nb ~ U{32..256}, and 1 or 6 core
