@@ -82,8 +82,11 @@ typedef struct {
   int n_bands;           /* conduction bands Nb                                     */
   int nx[3];             /* real-space grid per cell; Nx = nx0*nx1*nx2              */
   int n_proj;            /* local-basis functions Np (0: no short-range term)      */
-  int max_vec;           /* largest n_vec processed in one pass (0 -> 1); larger
-                            batches are processed in chunks of max_vec            */
+  int max_vec;           /* largest n_vec processed in one pass (0 -> 1, at most
+                            4096; split-bf16: max_vec*n_alpha <= 4096); larger
+                            batches are processed in chunks of max_vec.  Wide
+                            passes (2*max_vec*n_alpha > 256 operand rows) run
+                            the tensor-core contractions in 256-row N tiles   */
   double kshift[3];      /* mesh shift s_d in units of the k spacing (0 = Gamma)   */
   const bse_c128* u;     /* [Nk][Nx][Nb] u_nk(x), columns orthonormal per k        */
   const double* e_nk;    /* [Nk][Nb] band energies, eV                             */
@@ -189,6 +192,42 @@ typedef enum { BSE_PRECOND_NONE = 0, BSE_PRECOND_JACOBI = 1, BSE_PRECOND_MLP = 2
 bse_status bse_gmres(bse_handle* h, const bse_c128* b, const bse_c128* z, int n_z, double rtol,
                      int restart, int max_iter, int precond, bse_c128* x, int* iters,
                      double* rel_resid);
+
+/* RIXS two-step (resonant inelastic x-ray scattering, named in the paper's
+ * abstract and Sec. 5 as the next use of this machinery; the final-state
+ * Hamiltonian is not given there).  Reading: the final state has the
+ * core-hole Hamiltonian's form with the hole index running over n_v localised
+ * valence states -- `val` is a handle set up with n_alpha = n_v on the same k
+ * mesh and bands as `core` -- and the emission moves the hole while the
+ * photo-electron (n, k) stays.  For every incoming shift z_j = omega_in + i
+ * Gamma_c (z_in [n_z]):
+ *   x_j = (z_j - H_core)^{-1} b          GMRES on (H_core - z_j) x' = b as in
+ *                                        bse_gmres (x_0 = 0; precond, rtol,
+ *                                        restart, max_iter as there), x = -x'
+ *   y_j = (D (x) I) x_j                  y[v][kn] = sum_alpha D[v][alpha] x[alpha][kn]
+ *   Haydock on H_val from y_j            n_steps steps, no re-orthogonalisation
+ * and the RIXS spectrum at energy loss w is
+ *   sigma_j(w) = -(1/pi) bcoef[j][0]^2 Im g_j(w + i Gamma_f)
+ * (bse_cf_spectrum on a, bcoef, steps_done).  b [N_core], d_em [n_v][n_alpha]
+ * (bse_c128), a [n_z][n_steps], bcoef [n_z][n_steps+1], steps_done [n_z],
+ * iters [n_z], rel_resid [n_z]: host or device memory.  Allocates the n_z
+ * intermediate and final-state vectors.  Returns BSE_ERR_INVALID_ARG for a
+ * NULL argument or handles on different meshes/bands/devices,
+ * BSE_ERR_NOT_CONVERGED if a GMRES solve stopped at max_iter (the outputs are
+ * still written), BSE_ERR_BREAKDOWN if a final-state recursion stopped early
+ * (valid outputs), and errors of the two drivers otherwise. */
+bse_status bse_rixs(bse_handle* core, bse_handle* val, const bse_c128* b, const bse_c128* z_in, int n_z,
+                    const bse_c128* d_em, double rtol, int restart, int max_iter, int precond, int n_steps,
+                    double* a, double* bcoef, int* steps_done, int* iters, double* rel_resid);
+
+/* Emission step of the RIXS two-step alone (device arrays, work on `stream`,
+ * NULL = legacy default; returns without waiting):
+ *   y[z][v][kn] = sum_alpha d_em[v][alpha] x[z][alpha][kn],
+ * x [n_z][n_alpha][n_kb], y [n_z][n_v][n_kb], d_em [n_v][n_alpha], all
+ * complex128 device memory; 1 <= n_v, n_alpha <= 16, 1 <= n_z <= 65535.
+ * BSE_ERR_INVALID_ARG for bad sizes or non-device arrays. */
+bse_status bse_rixs_emission(const bse_c128* d_em, int n_v, int n_alpha, long long n_kb, const bse_c128* x,
+                             int n_z, bse_c128* y, void* stream);
 
 /* ---- learned GMRES preconditioner (no counterpart in the paper) ----------
  * For every row j = (alpha, n, k) and shift z = omega + i*Gamma, 12 features

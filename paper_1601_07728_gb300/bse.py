@@ -26,7 +26,7 @@ EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", 
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
            "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc",
            "bse_mlp_n_params", "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_params", "bse_mlp_outputs",
-           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0", "bse_set_wait_limit"]
+           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0", "bse_set_wait_limit", "bse_rixs", "bse_rixs_emission"]
 KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
 
 
@@ -119,6 +119,10 @@ def lib():
     L.bse_set_tiles.restype = ci
     L.bse_set_wait_limit.argtypes = [vp, cd]
     L.bse_set_wait_limit.restype = ci
+    L.bse_rixs.argtypes = [vp, vp, vp, vp, ci, vp, cd, ci, ci, ci, ci, vp, vp, vp, vp, vp]
+    L.bse_rixs.restype = ci
+    L.bse_rixs_emission.argtypes = [vp, ci, ci, cll, vp, ci, vp, vp]
+    L.bse_rixs_emission.restype = ci
     L.bse_local_projection.argtypes = [vp, vp, vp, ci, vp, vp, ci, cd, vp, vp]
     L.bse_local_projection.restype = ci
     L.bse_screening_chi0.argtypes = [vp, vp, ci, ci, cd, vp, vp, ci, vp, vp, vp]
@@ -421,7 +425,10 @@ def _chk(st):
 
 
 def attach_mlp(sysg, mlp):
+    """Attach (or detach with None) the network GMRES uses with precond="mlp".
+    The System keeps a reference, so the network outlives its use by the handle."""
     sysg._check(lib().bse_gmres_set_mlp(sysg.h, mlp.h if mlp is not None else None))
+    sysg._mlp = mlp
 
 
 def local_projection(u, nk, nx, f, dv, kshift=(0.0, 0.0, 0.0), stream=None):
@@ -474,3 +481,33 @@ def short_range_noalloc(a_proj, m_sr, psi, out, n_alpha, stream=None):
     n_vec = 1 if psi.ndim == 1 else psi.shape[0]
     return lib().bse_short_range_noalloc(_ptr(a_proj), _ptr(m_sr), _ptr(psi), _ptr(out), int(n_alpha), int(n_kb),
                                          int(n_proj), int(n_vec), stream)
+
+
+def rixs(core, val, b, z_in, d_em, n_steps, rtol=1e-6, restart=30, max_iter=3000, precond="none"):
+    """RIXS two-step through bse_rixs: returns (a [nz][n], bcoef [nz][n+1], steps [nz],
+    iters [nz], rel_resid [nz], status).  core and val are Systems on the same mesh."""
+    z = np.ascontiguousarray(np.atleast_1d(z_in), dtype=np.complex128)
+    nz = z.shape[0]
+    d = np.ascontiguousarray(d_em, dtype=np.complex128)
+    if d.shape != (val.dim // (core.dim // d.shape[1]), d.shape[1]):
+        raise ValueError("d_em must be [n_v][n_alpha] of the two systems")
+    a = np.zeros((nz, n_steps))
+    bc = np.zeros((nz, n_steps + 1))
+    steps = np.zeros(nz, dtype=np.int32)
+    it = np.zeros(nz, dtype=np.int32)
+    rel = np.zeros(nz)
+    st = lib().bse_rixs(core.h, val.h, _buf(b, "complex128", core.dim, "b"), _ptr(z), nz, _ptr(d), float(rtol),
+                        int(restart), int(max_iter), PRECOND[precond] if isinstance(precond, str) else int(precond),
+                        int(n_steps), _ptr(a), _ptr(bc), _ptr(steps), _ptr(it), _ptr(rel))
+    if st not in (BSE_OK, BSE_ERR_BREAKDOWN, BSE_ERR_NOT_CONVERGED):
+        raise BSEError(st, lib().bse_last_error(core.h).decode())
+    return a, bc, steps, it, rel, st
+
+
+def rixs_emission(d_em, x, y, n_alpha, stream=None):
+    """y = (D (x) I) x on device tensors through bse_rixs_emission; returns the status."""
+    n_v = d_em.shape[0]
+    n_z = 1 if x.ndim == 1 else x.shape[0]
+    n_kb = (x.numel() if hasattr(x, "numel") else x.size) // (n_z * n_alpha)
+    return lib().bse_rixs_emission(_ptr(d_em), int(n_v), int(n_alpha), int(n_kb), _ptr(x), int(n_z), _ptr(y),
+                                   stream)

@@ -73,6 +73,10 @@ CONFIGS = {
     # L2,3 edge with multiplets: 6 core states, 8^3 k, 64 bands, 16^3 grid
     "l23_multiplet": dict(id=2, n_alpha=6, nk=(8, 8, 8), n_bands=64, nx=(16, 16, 16),
                           cell=7.4, eps=5.0, n_proj=36, so_split=5.7, m_scale=0.5),
+    # the L2,3 physics on a smaller mesh (4^3 k, 32 bands, 8^3 grid): training
+    # variants and small profiling cases
+    "l23_reduced": dict(id=2, n_alpha=6, nk=(4, 4, 4), n_bands=32, nx=(8, 8, 8),
+                        cell=7.4, eps=5.0, n_proj=36, so_split=5.7, m_scale=0.5),
     # SrTiO3 4x4x4-like supercell: 2^3 k, 1024 bands, 48^3 grid
     "supercell_48": dict(id=4, n_alpha=6, nk=(2, 2, 2), n_bands=1024, nx=(48, 48, 48),
                          cell=29.5, eps=6.0, n_proj=36, so_split=5.7, m_scale=0.5),
