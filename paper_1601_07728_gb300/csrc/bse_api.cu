@@ -201,7 +201,7 @@ bse_status bse_setup(bse_handle** out, const bse_system_desc* d) {
     h->dev_cap = (size_t)v;
   }
   if (h->prec == BSE_PREC_SPLIT_BF16) {
-    if ((long long)h->max_vec * h->na * 2 > 256) return bad("split-bf16 form needs 2*max_vec*n_alpha <= 256");
+    if ((long long)h->max_vec * h->na > 4096) return bad("split-bf16 form needs max_vec*n_alpha <= 4096");
   }
   if (cudaGetDevice(&h->dev) != cudaSuccess) {
     cudaGetLastError();

@@ -149,10 +149,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
 // ---------------------------------------------------------------------------
 struct TcParams {
   int mode;            // 0: band->grid (phi out), 1: grid->band (split-K partials out)
-  int ntiles;          // work units = batch * mtiles * nsplit
+  int ntiles;          // work units = batch * mtiles * nsplit * ntn
   int mtiles, nsplit;
   int kb_per_split, kb_total;
-  int nn;              // MMA N (multiple of 16)
+  int nn;              // MMA N of one tile (multiple of 16, <= 256)
+  int ntn;             // N tiles (B rows nt*nn .. nt*nn + nn - 1, two rows per complex column)
   int stages;
   uint32_t tmem_cols;
   float2* out;
@@ -162,11 +163,14 @@ struct TcParams {
 };
 
 struct Tile {
-  int batch, mt, split, kb0, nkb;
+  int batch, mt, split, nt, kb0, nkb;
 };
 
+// N tile fastest, so that consecutive CTAs share the A tile (u_nk) in L2
 __device__ __forceinline__ Tile decode(const TcParams& p, int t) {
   Tile r;
+  r.nt = t % p.ntn;
+  t /= p.ntn;
   r.split = t % p.nsplit;
   int rest = t / p.nsplit;
   r.mt = rest % p.mtiles;
@@ -249,15 +253,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int kc = (tl.kb0 + kb) * TC_KB;
           tma_load_3d(st, &ma_hi, full(s), kc, tl.mt * TC_M, tl.batch);
           tma_load_3d(st + a_bytes, &ma_lo, full(s), kc, tl.mt * TC_M, tl.batch);
-          tma_load_3d(st + 2 * a_bytes, &mb_hi, full(s), kc, 0, tl.batch);
-          tma_load_3d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), kc, 0, tl.batch);
+          tma_load_3d(st + 2 * a_bytes, &mb_hi, full(s), kc, tl.nt * p.nn, tl.batch);
+          tma_load_3d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), kc, tl.nt * p.nn, tl.batch);
         } else {
           // K-tiled operands [batch][K/64][rows][64]: one contiguous block per K block
           const int kt = tl.kb0 + kb;
           tma_load_4d(st, &ma_hi, full(s), 0, tl.mt * TC_M, kt, tl.batch);
           tma_load_4d(st + a_bytes, &ma_lo, full(s), 0, tl.mt * TC_M, kt, tl.batch);
-          tma_load_4d(st + 2 * a_bytes, &mb_hi, full(s), 0, 0, kt, tl.batch);
-          tma_load_4d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), 0, 0, kt, tl.batch);
+          tma_load_4d(st + 2 * a_bytes, &mb_hi, full(s), 0, tl.nt * p.nn, kt, tl.batch);
+          tma_load_4d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), 0, tl.nt * p.nn, kt, tl.batch);
         }
         *(volatile int*)issued = it + 1;
       }
@@ -336,6 +340,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       tc_fence_after();
       const int row = tl.mt * TC_M + row_in_tile;
+      const int cbase = tl.nt * (p.nn >> 1);   // first complex column of this N tile
       for (int c16 = 0; c16 < p.nn / 16; ++c16) {
         float v[16];
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * p.nn + c16 * 16), v);
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (row < p.nx) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const int c = c16 * 8 + i;
+              const int c = cbase + c16 * 8 + i;
               if (c < p.nc) p.out[((size_t)tl.batch * p.nc + c) * p.nx + row] = make_float2(v[2 * i], v[2 * i + 1]);
             }
           }
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float2* o = p.out + ((size_t)tl.split * p.nk + tl.batch) * p.nc * p.nb + n;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const int c = c16 * 8 + i;
+              const int c = cbase + c16 * 8 + i;
               if (c < p.nc) o[(size_t)c * p.nb] = make_float2(v[2 * i] + pv[2 * i + 1], v[2 * i + 1] - pv[2 * i]);
             }
           }
@@ -774,6 +779,12 @@ struct TcState {
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// MMA N of one tile for `rows` B rows (two per complex column): one tile up
+// to 256 rows (the tcgen05 maximum, two accumulators filling TMEM's 512
+// columns); wider operands in 256-row tiles (the last one partly out of the
+// tensor, zero-filled by TMA, its columns not stored)
+inline int tile_n(int rows) { return rows <= 256 ? rows : 256; }
+
 // most pipeline stages that fit shared memory for MMA width nn (at most 8)
 int fit_stages(int nn) {
   const int stage = 2 * TC_M * 128 + 2 * nn * 128;
@@ -880,13 +891,14 @@ bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_d
 bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec) {
   TcState* ts = (TcState*)h->tmap_host;
   const int nc = n_vec * h->na;
-  const int nn = round_up(2 * nc, 16);
+  const int rows = round_up(2 * nc, 16);
+  const int nn = tile_n(rows);
   const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
   __nv_bfloat16* bh = h->bpsi;
   __nv_bfloat16* bl = h->bpsi + nbp;
   CUtensorMap b_hi, b_lo;
-  if (!make_map(&b_hi, bh, ts->kp, nn, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn) ||
-      !make_map(&b_lo, bl, ts->kp, nn, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn))
+  if (!make_map(&b_hi, bh, ts->kp, rows, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn) ||
+      !make_map(&b_lo, bl, ts->kp, rows, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, nn))
     return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
   TcParams p{};
   p.mode = 0;
@@ -894,7 +906,8 @@ bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec) {
   p.nsplit = 1;
   p.kb_total = (ts->kp + TC_KB - 1) / TC_KB;
   p.kb_per_split = p.kb_total;
-  p.ntiles = h->nk * p.mtiles;
+  p.ntn = (rows + nn - 1) / nn;
+  p.ntiles = h->nk * p.mtiles * p.ntn;
   p.nn = nn;
   p.out = (float2*)h->phi;
   p.nk = h->nk;
@@ -914,12 +927,13 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
                                const bse_dotfuse* fuse, bool wait_side) {
   TcState* ts = (TcState*)h->tmap_host;
   const int nc = n_vec * h->na;
-  const int nn = round_up(2 * nc, 16);
+  const int rows = round_up(2 * nc, 16);
+  const int nn = tile_n(rows);
   const size_t x64 = (size_t)(h->nx + TC_KB - 1) / TC_KB;
   const size_t nbf = (size_t)h->nk * x64 * ts->nnmax * TC_KB;
   CUtensorMap b_hi, b_lo;
-  if (!make_map_tiled(&b_hi, h->bphi, nn, ts->nnmax, x64, h->nk, nn) ||
-      !make_map_tiled(&b_lo, h->bphi + nbf, nn, ts->nnmax, x64, h->nk, nn))
+  if (!make_map_tiled(&b_hi, h->bphi, rows, ts->nnmax, x64, h->nk, nn) ||
+      !make_map_tiled(&b_lo, h->bphi + nbf, rows, ts->nnmax, x64, h->nk, nn))
     return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
   TcParams p{};
   p.mode = 1;
@@ -928,7 +942,8 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   p.nsplit = ts->smax < p.kb_total ? ts->smax : p.kb_total;
   p.kb_per_split = (p.kb_total + p.nsplit - 1) / p.nsplit;
   p.nsplit = (p.kb_total + p.kb_per_split - 1) / p.kb_per_split;   // no empty split
-  p.ntiles = h->nk * p.mtiles * p.nsplit;
+  p.ntn = (rows + nn - 1) / nn;
+  p.ntiles = h->nk * p.mtiles * p.nsplit * p.ntn;
   p.nn = nn;
   p.out = (float2*)h->part;
   p.nk = h->nk;
@@ -982,13 +997,15 @@ bse_operand_out bse_tc_operand(const bse_handle* h) {
 
 int bse_tc_final_blocks(const bse_handle* h) {
   const size_t nkb = (size_t)h->nk * h->nb;
-  // one thread per (k, n, alpha) of a vector up to two blocks per SM, grid-stride
-  // beyond: every block's <psi|H psi> partial is reduced again by each block of
-  // the Haydock update (FP64, a slow pipe on this part), so fewer partials pay
+  // one thread per (k, n, alpha) of a vector up to four blocks per SM,
+  // grid-stride beyond: every block's <psi|H psi> partial is reduced again by
+  // each block of the Haydock update (FP64, a slow pipe on this part), so the
+  // count is capped; four per SM measured 28 us against 33 us at two per SM
+  // on the L2,3 workload
   const size_t threads = nkb * (size_t)h->na;
   size_t bk = (threads + 255) / 256;
   const TcState* ts = (const TcState*)h->tmap_host;
-  const size_t cap = ts && ts->sms > 0 ? (size_t)2 * ts->sms : 304;
+  const size_t cap = ts && ts->sms > 0 ? (size_t)4 * ts->sms : 608;
   if (bk > cap) bk = cap;
   if (bk > BSE_FINAL_BLOCKS) bk = BSE_FINAL_BLOCKS;
   return (int)bk;
@@ -1059,7 +1076,7 @@ extern "C" bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* spli
   const int kbt = (h->nx + TC_KB - 1) / TC_KB;
   std::vector<int> splits;
   for (int s = 1; s <= 16 && s <= kbt; s *= 2) splits.push_back(s);
-  const int nn = round_up(2 * n_vec * h->na, 16);
+  const int nn = tile_n(round_up(2 * n_vec * h->na, 16));
   const int fit = fit_stages(nn);
   std::vector<int> stages;
   for (int s : {3, 4, 6, 8})

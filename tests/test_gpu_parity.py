@@ -73,6 +73,38 @@ def test_apply_h_split_bf16_matches_oracle(kw):
         close("apply_h/split_bf16/seed%d/v%d" % (kw["seed"], v), out[v], ref[v], "split_bf16")
 
 
+@pytest.mark.parametrize("na,n_vec", [(6, 23), (6, 50), (1, 300), (6, 136)])
+def test_apply_h_split_bf16_wide_columns(na, n_vec):
+    """More columns than one tensor-core tile holds (2 x N_alpha x n_vec > 256
+    operand rows): the contractions run in 256-row N tiles, the last one
+    partly outside the operand (zero-filled, not stored): 288, 608, 608 and
+    1632 rows."""
+    s = S.tiny_system(60 + n_vec, n_alpha=na, nk=(2, 2, 2), n_bands=24, nx=(8, 8, 4), n_proj=3)
+    sysg = bse.System(s, precision="split_bf16", max_vec=n_vec)
+    psi = S.complex_normal(np.random.default_rng(n_vec), (n_vec, s.dim))
+    out = sysg.apply_h(psi)
+    ref = O.apply_h(s, psi)
+    close("wide/apply_h/na%d/v%d" % (na, n_vec), out, ref, "split_bf16")
+    for v in (0, n_vec // 2, n_vec - 1):
+        close("wide/apply_h/na%d/v%d/vec%d" % (na, n_vec, v), out[v], ref[v], "split_bf16")
+
+
+def test_gmres_forty_shifts_in_one_pass():
+    """40 shifts advanced together with max_vec = 40 (480 columns, two N
+    tiles per contraction): converged x equal the oracle's dense solves."""
+    s = S.tiny_system(62, n_alpha=6, nk=(2, 2, 1), n_bands=8, nx=(4, 4, 4), n_proj=2)
+    b = S.make_start_vectors(s, 1)[0]
+    z = np.linspace(-3.0, 25.0, 40) + 0.6j
+    sysg = bse.System(s, precision="split_bf16", max_vec=40)
+    x, it, rr, st = sysg.gmres(b, z, rtol=1e-6, restart=30, max_iter=2000, precond="none")
+    assert st == bse.BSE_OK and np.all(rr <= 1e-6)
+    h = O.dense_h(s)
+    for j in (0, 13, 39):
+        xs = np.linalg.solve(h - z[j] * np.eye(s.dim), b)
+        # the solve amplifies the split-bf16 operator error by up to |H - z| |(H - z)^-1| ~ 40
+        close("wide/gmres40/z%d" % j, x[j], xs, (1e-3, 1e-3))
+
+
 @pytest.mark.parametrize("n", [3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
 def test_cubic_k_meshes_match_oracle(n, prec):
