@@ -66,6 +66,8 @@ def parse():
                    help="shifts (every n-th of the GMRES set) also solved by the plain FP64 form (0 = skip)")
     p.add_argument("--train-omega", type=int, default=8, help="training shifts of the learned preconditioner")
     p.add_argument("--train-epochs", type=int, default=10)
+    p.add_argument("--train-systems", type=int, default=2,
+                   help="seeded variants of the workload the preconditioner is trained on (0: the measured system)")
     p.add_argument("--fp64-steps", type=int, default=10,
                    help="captured Haydock steps of the plain FP64 form on the same workload (0 = skip)")
     p.add_argument("--supercell-steps", type=int, default=20,
@@ -228,6 +230,23 @@ def cpu_oracle_rate(s, b, seconds, max_steps=None):
         el = time.perf_counter() - t0
         if el >= seconds or (max_steps and n >= max_steps):
             return n, el
+
+
+def oracle_rate_one_thread(workload, steps=3):
+    """The oracle on one host thread: this script's reference arm in a child
+    process with every BLAS / OpenMP pool pinned to one thread."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("RANK", None)
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--workload", workload,
+                            "--steps", str(steps), "--warmup", "1"], env=env, capture_output=True, text=True,
+                           timeout=600)
+        line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
+        return float(json.loads(line)["value"])
+    except Exception:
+        return None
 
 
 def reference_arm(args):
@@ -462,16 +481,37 @@ def main():
         if args.train_omega > 0:
             step = (zs[1].real - zs[0].real) if n_om > 1 else 1.0
             zt = np.linspace(-5.0 + 0.5 * step, 30.0 - 0.5 * step, args.train_omega) + 0.5j
+            # training systems: seeded variants of the workload (other u_nk, band
+            # energies, projectors and couplings), never the measured system
+            if args.train_systems > 0:
+                tr_sys, tr_b = [], []
+                for k in range(1, args.train_systems + 1):
+                    sk = S.make_system_device(dict(S.CONFIGS[args.workload]), site=k, name=args.workload)
+                    tr_sys.append(bse.System(sk, precision=args.precision, max_vec=args.gmres_chunk,
+                                             stream=stream.cuda_stream))
+                    tr_b.append(S.make_start_vectors(sk, 1)[0])
+                    del sk
+                torch.cuda.empty_cache()
+                trained_on = "seeded variants (sites 1..%d) of the workload; evaluated on the held-out site 0" % (
+                    args.train_systems)
+            else:
+                tr_sys, tr_b = [sys_g], [b]
+                trained_on = "the measured system itself"
             torch.cuda.synchronize()
             t_tr = time.perf_counter()
-            hist = net.train([sys_g], [b], zt, epochs=args.train_epochs, batch=1, lr=1e-3, seed=1, steps=10)
+            hist = net.train(tr_sys, tr_b, zt, epochs=args.train_epochs, batch=1, lr=1e-3, seed=1, steps=10)
             torch.cuda.synchronize()
             t_tr = time.perf_counter() - t_tr
+            for g_ in tr_sys:
+                if g_ is not sys_g:
+                    g_.close()
+            del tr_sys
             gm["mlp_trained"] = leg(sys_g, "mlp", zs, xg)
             gm["mlp_trained"]["training"] = {
                 "seconds": t_tr, "shifts": args.train_omega, "epochs": args.train_epochs,
+                "systems": max(1, args.train_systems), "trained_on": trained_on,
                 "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1]),
-                "note": "shifts held out from the measured set (midpoints); training timed separately"}
+                "note": "training shifts are the midpoints between measured shifts; training timed separately"}
         bse.attach_mlp(sys_g, None)
         del net
         if args.gmres_fp64_omega > 0:
@@ -603,6 +643,11 @@ def main():
             cpu = {"value": ns / el2, "unit": "matvecs/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": "%d FP64 NumPy oracle Haydock steps of the same workload (%.1f s; BLAS-threaded "
                              "matmuls, single-threaded FFTs)" % (ns, el2)}
+            # the same oracle on one thread, and on the 1s workload
+            cpu["one_thread_matvecs_per_s"] = oracle_rate_one_thread(args.workload)
+            s1 = S.make_system("k_edge_small")
+            n1, e1 = cpu_oracle_rate(s1, S.make_start_vectors(s1, 1)[0], 2.0)
+            cpu["k_edge_small_matvecs_per_s"] = n1 / e1
         dtype = {"fp64": "f64", "fp32": "f32", "split_bf16": "bf16x3"}[args.precision]
         line = {
             "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": world, "steps": K, "warmup": W,
