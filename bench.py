@@ -59,15 +59,20 @@ def parse():
                    help="tensor-core tiles of the headline run: auto (timed search) or SPLIT_K,STAGES")
     p.add_argument("--polarisations", type=int, default=3,
                    help="start vectors of the batched-polarisation Haydock measurement (<= 1: skip)")
-    p.add_argument("--gmres-omega", type=int, default=40, help="shifts in the GMRES measurement (0 = skip)")
+    p.add_argument("--gmres-omega", type=int, default=200, help="shifts in the GMRES measurement (0 = skip)")
     p.add_argument("--gmres-max-iter", type=int, default=2000)
-    p.add_argument("--gmres-chunk", type=int, default=10, help="systems per batched H application")
+    p.add_argument("--gmres-chunk", type=int, default=200, help="systems per batched H application")
+    p.add_argument("--gmres-jacobi-omega", type=int, default=40,
+                   help="shifts (every n-th of the GMRES set) of the Jacobi-preconditioned comparison")
     p.add_argument("--gmres-fp64-omega", type=int, default=4,
                    help="shifts (every n-th of the GMRES set) also solved by the plain FP64 form (0 = skip)")
-    p.add_argument("--train-omega", type=int, default=8, help="training shifts of the learned preconditioner")
+    p.add_argument("--train-omega", type=int, default=16, help="training shifts of the learned preconditioner")
     p.add_argument("--train-epochs", type=int, default=10)
     p.add_argument("--train-systems", type=int, default=2,
                    help="seeded variants of the workload the preconditioner is trained on (0: the measured system)")
+    p.add_argument("--apply-only", action="store_true",
+                   help="time --steps applications of H to --apply-vectors vectors at once and exit")
+    p.add_argument("--apply-vectors", type=int, default=200)
     p.add_argument("--fp64-steps", type=int, default=10,
                    help="captured Haydock steps of the plain FP64 form on the same workload (0 = skip)")
     p.add_argument("--supercell-steps", type=int, default=20,
@@ -276,6 +281,40 @@ def reference_arm(args):
     return 0
 
 
+def apply_only(args, s, dist, world, rank):
+    """H psi on --apply-vectors vectors in one pass (all columns of the
+    tensor-core contractions at once), --steps timed applications after
+    --warmup: matvecs/s and the FLOP rate of the two contractions."""
+    import numpy as np
+    import torch
+    from paper_1601_07728_gb300 import bse, synth as S
+    nv = args.apply_vectors
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    g = bse.System(s, precision=args.precision, max_vec=nv, stream=stream.cuda_stream)
+    psi = torch.from_numpy(S.complex_normal(np.random.default_rng(0), (nv, s.dim))).to("cuda")
+    out = torch.empty_like(psi)
+    for _ in range(max(args.warmup, 1)):
+        g.apply_h(psi, out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.apply_h(psi, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
+    fl = 2 * 8.0 * s.n_k * s.n_x * s.n_bands * s.n_alpha * nv
+    if rank == 0:
+        print(json.dumps({"mode": "apply_only", "workload": args.workload, "precision": args.precision,
+                          "vectors": nv, "columns": nv * s.n_alpha, "ms_per_application": ms,
+                          "matvecs_per_s": job_rate(nv, ms / 1e3, world),
+                          "contraction_tflops": fl / (ms / 1e3) / 1e12}), flush=True)
+    g.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -303,6 +342,8 @@ def main():
 
     s = S.make_system(args.workload)
     b = S.make_start_vectors(s, 1)[0]
+    if args.apply_only:
+        return apply_only(args, s, dist, world, rank)
     # a dedicated (capturable) stream: the library records each Haydock run as one CUDA graph
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -471,7 +512,10 @@ def main():
 
         gm["none"] = leg(sys_g, "none", zs, xg)
         sig_none = sigma_of(xg)
-        gm["jacobi"] = leg(sys_g, "jacobi", zs, xg)
+        # Jacobi on an evenly spaced subset (it converges slowly at interior shifts)
+        selj = np.linspace(0, n_om - 1, min(args.gmres_jacobi_omega, n_om)).round().astype(int)
+        gm["jacobi"] = leg(sys_g, "jacobi", zs[selj], xg[:len(selj)])
+        gm["jacobi"]["omega_subset"] = "every %.1f-th shift of the set" % (n_om / max(len(selj), 1))
         # learned preconditioner: the network's prior (last layer zero: the damped
         # diagonal) and the network after training on the GPU at shifts between the
         # measured ones (residual probes of plain GMRES(30), 10-step minimal-residual loss)
@@ -487,7 +531,7 @@ def main():
                 tr_sys, tr_b = [], []
                 for k in range(1, args.train_systems + 1):
                     sk = S.make_system_device(dict(S.CONFIGS[args.workload]), site=k, name=args.workload)
-                    tr_sys.append(bse.System(sk, precision=args.precision, max_vec=args.gmres_chunk,
+                    tr_sys.append(bse.System(sk, precision=args.precision, max_vec=min(args.gmres_chunk, 16),
                                              stream=stream.cuda_stream))
                     tr_b.append(S.make_start_vectors(sk, 1)[0])
                     del sk
@@ -512,6 +556,41 @@ def main():
                 "systems": max(1, args.train_systems), "trained_on": trained_on,
                 "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1]),
                 "note": "training shifts are the midpoints between measured shifts; training timed separately"}
+        # one restart cycle (30 iterations) of the trained-network solve with the
+        # library's launch timing on: where GMRES time goes, and the FLOP rate of
+        # the band->grid contraction at this column count (first cycle: every
+        # shift active, so each H application covers min(chunk, n_omega) shifts)
+        sys_g.profile(True)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        _, it_c, _, _ = sys_g.gmres(db, zs, rtol=1e-6, restart=30, max_iter=30, precond="mlp", x=xg)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cyc_ms = c0.elapsed_time(c1)
+        prof_g = sys_g.profile_read()
+        sys_g.profile(False)
+        n_apply = int(np.sum(it_c)) + n_om                   # Arnoldi applications + one true residual each
+        fl = 8.0 * s.n_k * s.n_x * s.n_bands * s.n_alpha * n_apply   # real flops of one contraction over the cycle
+        nb2g, tb2g = prof_g["band_to_grid"]
+        peaks_d = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks_d = json.load(f)
+        except Exception:
+            pass
+        bf16_sus = float(peaks_d.get("bf16_tflops_sustained", 1700.0))
+        alg_tf = fl / (tb2g / 1e3) / 1e12 if tb2g > 0 else None
+        gm["one_cycle_breakdown"] = {
+            "ms": cyc_ms, "h_applications": n_apply, "columns_per_pass": min(args.gmres_chunk, n_om) * s.n_alpha,
+            "kernels_ms": {k: round(v[1], 3) for k, v in prof_g.items() if v[0]},
+            "band_to_grid_roofline": {
+                "bound": "tensor", "unit": "TFLOP/s", "alg_tflops": alg_tf,
+                "tensor_tflops": None if alg_tf is None else 3 * alg_tf,
+                "peak": bf16_sus, "peak_kind": "measured bf16 sustained" if peaks_d else "fallback",
+                "frac": None if alg_tf is None else 3 * alg_tf / bf16_sus, "launches": nb2g,
+                "note": "split-bf16 runs three bf16 MMAs per product (hi*hi + hi*lo + lo*hi): tensor work "
+                        "= 3 x the complex contraction's 8 real flops per MAC"}}
         bse.attach_mlp(sys_g, None)
         del net
         if args.gmres_fp64_omega > 0:
