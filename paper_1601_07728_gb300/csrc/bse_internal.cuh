@@ -148,6 +148,15 @@ bse_status bse_cuda_check(bse_handle* h, cudaError_t e, const char* what);
 // setup kernels (k_setup.cu)
 bse_status bse_setup_device(bse_handle* h, const bse_system_desc* d);
 
+// Where a Haydock update writes the next step's band->grid operand (bf16
+// hi/lo [Nk][Nrow][K_p]) and FP32 psi; hi == nullptr: not written.
+struct bse_operand_out {
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;
+  float2* psi_f = nullptr;
+  int nk = 0, nb = 0, na = 0, kp = 0, nnmax = 0;
+};
+
 // Haydock hook fused into the last kernel of H psi: a[v][i] = Re <psi_v | H psi_v>
 // from per-block partial sums; the last block to finish (counter) reduces them
 // in a fixed order and resets the counter.
@@ -176,16 +185,20 @@ struct bse_dotfuse {
   // unnormalised, so the operand pass is skipped and the grid->band epilogue
   // does the lazy normalisation (every term it adds is linear in psi)
   bool operand_ready = false;
+  // fused update (tensor-core form, N_alpha in {1, 6}, whole grid resident):
+  // after its dot partials the epilogue meets every other block at a bounded
+  // grid barrier, reduces a_i itself and applies w = H v_i - a_i v_i - b_i
+  // v_{i-1} in place of the separate Haydock update kernel, writing the |w|^2
+  // partials (upart [n_vec][gridDim.x]) and the next operand (op)
+  bool fused_update = false;
+  const double2* vprev = nullptr;   // v_{i-1}
+  double2* upart = nullptr;
+  unsigned* barrier = nullptr;      // {arrivals, generation}; arrivals zero between uses
+  bse_operand_out op;
 };
+// status bit of a grid barrier that gave up (BSE_ERR_TIMEOUT)
+#define BSE_ST_TIMEOUT 4
 
-// Where a Haydock update writes the next step's band->grid operand (bf16
-// hi/lo [Nk][Nrow][K_p]) and FP32 psi; hi == nullptr: not written.
-struct bse_operand_out {
-  __nv_bfloat16* hi = nullptr;
-  __nv_bfloat16* lo = nullptr;
-  float2* psi_f = nullptr;
-  int nk = 0, nb = 0, na = 0, kp = 0, nnmax = 0;
-};
 // A[p][k][n] = dv sum_x conj(f_p(x)) e^{ik.x} u_nk(x) on device arrays (k_local.cu)
 bse_status bse_local_projection_device(const double2* u, const int* nk, const int* nx, int nb, const double* kshift,
                                        const double2* f, int np, double dv, double2* a, cudaStream_t st);
@@ -208,6 +221,9 @@ bse_status bse_tc_prepare(bse_handle* h);
 bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_dotfuse* fuse);
 // blocks per vector of the grid->band epilogue (the number of <psi|H psi> partials it writes)
 int bse_tc_final_blocks(const bse_handle* h);
+// true if the fused epilogue + Haydock update can run for n_vec vectors (the
+// whole grid of the epilogue is resident at once, so its barrier completes)
+bool bse_tc_fused_update_ok(const bse_handle* h, int n_vec);
 bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec);
 bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
                                const bse_dotfuse* fuse, bool wait_side);

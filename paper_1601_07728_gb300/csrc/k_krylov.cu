@@ -17,7 +17,7 @@ constexpr int RB = 256;      // threads per reduction block
 constexpr int NBLK = 296;    // partial-sum blocks per vector (2 x 148)
 constexpr int UBLK = 296;    // blocks per vector of the Haydock update (its |w|^2 partials are reduced again by every block of the next operand pass)
 
-enum { ST_BREAKDOWN = 1, ST_NAN = 2 };
+enum { ST_BREAKDOWN = 1, ST_NAN = 2, ST_TIMEOUT = BSE_ST_TIMEOUT };
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
@@ -692,15 +692,16 @@ __global__ void __launch_bounds__(RB) hay_update_deferred(double2* __restrict__ 
     const size_t o = (size_t)v * N + e;
     double2 ww = w[o];
     const double2 c = vc[o];
-    ww.x -= ai * c.x;
-    ww.y -= ai * c.y;
+    // explicit FMAs: the fused epilogue update computes the same bits
+    ww.x = fma(-ai, c.x, ww.x);
+    ww.y = fma(-ai, c.y, ww.y);
     if (i >= 1) {
       const double2 p = vp[o];
-      ww.x -= bi * p.x;
-      ww.y -= bi * p.y;
+      ww.x = fma(-bi, p.x, ww.x);
+      ww.y = fma(-bi, p.y, ww.y);
     }
     w[o] = ww;
-    acc += ww.x * ww.x + ww.y * ww.y;
+    acc = fma(ww.x, ww.x, fma(ww.y, ww.y, acc));
     if (op.hi) {
       const float re = (float)ww.x, im = (float)ww.y;
       op.psi_f[o] = make_float2(re, im);
@@ -755,8 +756,10 @@ __global__ void __launch_bounds__(RB) hay_norm_final(const double2* __restrict__
 
 namespace {
 // Grow-only Haydock workspace of a handle: three vectors, partial sums, flags.
+constexpr int HPART = UBLK > BSE_FINAL_BLOCKS ? UBLK : BSE_FINAL_BLOCKS;   // |w|^2 partials per vector
+
 size_t hay_ws_bytes(long long N, int n_vec) {
-  return 3 * (size_t)n_vec * N * sizeof(double2) + (size_t)n_vec * UBLK * sizeof(double2) +
+  return 3 * (size_t)n_vec * N * sizeof(double2) + (size_t)n_vec * HPART * sizeof(double2) +
          (size_t)n_vec * BSE_FINAL_BLOCKS * sizeof(double2) + 256 + (size_t)n_vec * sizeof(int) + 256;
 }
 
@@ -785,7 +788,7 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   {
     TRY(hay_reserve(h, n_vec));
     const size_t bv = 3 * (size_t)n_vec * N * sizeof(double2);
-    const size_t bp = (size_t)n_vec * UBLK * sizeof(double2);
+    const size_t bp = (size_t)n_vec * HPART * sizeof(double2);
     const size_t bf = (size_t)n_vec * BSE_FINAL_BLOCKS * sizeof(double2);
     char* p = (char*)h->ws;
     v3 = (double2*)p;
@@ -809,6 +812,15 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   const bse_operand_out opd = fused_op ? bse_tc_operand(h) : bse_operand_out();
   const int ublk = (int)std::min<long long>(UBLK, (N + RB - 1) / RB);
   const int nfb = fuse_a ? bse_tc_final_blocks(h) : 0;
+  // ... and, for one vector of a site running alone, the update itself runs
+  // inside the epilogue's grid after a bounded grid barrier (one launch less
+  // per step); its |w|^2 partials are then one per epilogue block
+  const bool fused_upd = fused_op && allow_graph && n_vec == 1 && bse_tc_fused_update_ok(h, n_vec);
+  // the separate deferred update runs on the epilogue's grid as well, so that
+  // both forms partition the vector and order every sum alike (a many-site
+  // run, which keeps the separate kernel, equals a single-site run bit for bit)
+  const int dblk = lazy_scale ? nfb : ublk;
+  const int nnorm = dblk;
   if (reorth) {
     // Gram-Schmidt partials need one row per basis vector
     TRY(dalloc(h, &partial, (size_t)n_vec * NBLK * (n_steps + 1) * sizeof(double2), "gs partials"));
@@ -867,11 +879,18 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
         f.deferred = true;
         if (i >= 1) {
           f.norm_part = hpart;
-          f.norm_n = ublk;
+          f.norm_n = nnorm;
           f.bco = b_d;
           f.active_rw = active;
           f.steps = steps_d;
           f.operand_ready = fused_op;
+        }
+        if (fused_upd) {
+          f.fused_update = true;
+          f.vprev = vp;
+          f.upart = hpart;
+          f.barrier = counters + 2;
+          f.op = i + 1 < n_steps ? opd : bse_operand_out();
         }
       }
       loop_status = bse_apply_device(h, vc, w, n_vec, &f);     // w = H v_i, a_i = Re <v_i|w>
@@ -882,9 +901,11 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
       BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_vec), RB, 0, st>>>(vc, N, w, N, N, hpart));
       BSE_PROF(h, BSE_K_RECURSION, hay_a_finalize<<<n_vec, RB, 0, st>>>(hpart, NBLK, a_d, n_steps, i, active, status));
     }
-    if (lazy_scale) {
+    if (fused_upd) {
+      // the epilogue already applied the update
+    } else if (lazy_scale) {
       BSE_PROF(h, BSE_K_RECURSION,
-               hay_update_deferred<<<dim3(ublk, n_vec), RB, 0, st>>>(
+               hay_update_deferred<<<dim3(dblk, n_vec), RB, 0, st>>>(
                    w, vc, vp, N, fpart, nfb, a_d, b_d, n_steps, i, active, hpart, status,
                    i + 1 < n_steps ? opd : bse_operand_out()));
     } else if (fuse_b) {
@@ -913,7 +934,7 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   }
   if (lazy_scale && loop_status == BSE_OK && n_steps >= 1) {
     BSE_PROF(h, BSE_K_RECURSION,
-             hay_norm_final<<<n_vec, RB, 0, st>>>(hpart, ublk, a_d, b_d, n_steps, n_steps, active, steps_d, status));
+             hay_norm_final<<<n_vec, RB, 0, st>>>(hpart, nnorm, a_d, b_d, n_steps, n_steps, active, steps_d, status));
   }
   if (!capturing) break;
   // end the capture on every path; launch the graph, or re-run eagerly
@@ -938,6 +959,7 @@ bse_status hay_finish(bse_handle* h, const int* status) {
   int hs = 0;
   TRY(bse_cuda_check(h, cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status copy"));
   TRY(bse_cuda_check(h, cudaStreamSynchronize(h->stream), "haydock sync"));
+  if (hs & ST_TIMEOUT) return bse_fail(h, BSE_ERR_TIMEOUT, "Haydock grid barrier timed out");
   if (hs & ST_NAN) return bse_fail(h, BSE_ERR_NAN, "non-finite Haydock coefficient");
   if (hs & ST_BREAKDOWN) return BSE_ERR_BREAKDOWN;
   return BSE_OK;

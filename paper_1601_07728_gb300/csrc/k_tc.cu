@@ -542,13 +542,128 @@ __device__ void fused_dot_tail(const bse_dotfuse& f, double dre, double dim) {
   if (threadIdx.x == 0) *f.counter = 0u;
 }
 
+// Grid-wide barrier of a resident grid (every block calls it once per use):
+// arrivals are counted in bar[0], the last block resets them and advances the
+// generation bar[1], which the others wait for -- at most 1 s of %globaltimer,
+// after which the block records BSE_ST_TIMEOUT and reports failure.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g0 = atomicOr(bar + 1, 0u);
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = gtime();
+      while (atomicOr(bar + 1, 0u) == g0) {
+        if (gtime() - t0 > 1000000000ull) {
+          good = 0;
+          atomicOr(status, BSE_ST_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ void split_pair(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Haydock update of vector v = blockIdx.y inside the epilogue's grid, after
+// the barrier: a_i from every block's <psi|H psi> partial (same order in every
+// block), w = H v_i - a_i v_i - b_i v_{i-1} over the vector (grid-stride), the
+// block's |w|^2 partial and the next step's band->grid operand from w.
+// act / bi: the vector's state as this block found it in the lazy
+// normalisation (every block computes the same values).
+__device__ void fused_update_phase(const bse_dotfuse& f, double2* __restrict__ w, const double2* __restrict__ vc,
+                                   long long n_per_vec, bool act, double bi) {
+  const int v = blockIdx.y;
+  if (!act) {
+    if (threadIdx.x == 0) f.upart[(size_t)v * gridDim.x + blockIdx.x] = make_double2(0.0, 0.0);
+    return;
+  }
+  __shared__ double ws_[8];
+  __shared__ double ai_s;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&f.partial[(size_t)v * gridDim.x + b].x);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) ws_[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += ws_[k];
+    ai_s = t;
+    if (blockIdx.x == 0) {
+      f.a[(size_t)v * f.a_stride + f.i] = t;
+      if (!isfinite(t)) atomicOr(f.status, 2);
+    }
+  }
+  __syncthreads();
+  const double ai = ai_s;
+  const bse_operand_out& op = f.op;
+  double acc = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_per_vec;
+       e += (long long)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)v * n_per_vec + e;
+    double2 ww = __ldcg(&w[o]);
+    const double2 c = __ldcg(&vc[o]);
+    // the same FMAs as the separate update kernel (bit-identical results)
+    ww.x = fma(-ai, c.x, ww.x);
+    ww.y = fma(-ai, c.y, ww.y);
+    if (f.i >= 1) {
+      const double2 p = f.vprev[o];
+      ww.x = fma(-bi, p.x, ww.x);
+      ww.y = fma(-bi, p.y, ww.y);
+    }
+    w[o] = ww;
+    acc = fma(ww.x, ww.x, fma(ww.y, ww.y, acc));
+    if (op.hi) {
+      const float re = (float)ww.x, im = (float)ww.y;
+      op.psi_f[o] = make_float2(re, im);
+      const int n = (int)(e % op.nb);
+      const long long ak = e / op.nb;
+      const int k = (int)(ak % op.nk);
+      const int cc = v * op.na + (int)(ak / op.nk);
+      __nv_bfloat16 h0, l0, h1, l1, h2, l2;
+      split_pair(re, h0, l0);
+      split_pair(-im, h1, l1);
+      split_pair(im, h2, l2);
+      const size_t o0 = ((size_t)k * op.nnmax + 2 * cc) * op.kp + 2 * n;
+      const size_t o1 = o0 + op.kp;
+      *reinterpret_cast<__nv_bfloat162*>(op.hi + o0) = __halves2bfloat162(h0, h1);
+      *reinterpret_cast<__nv_bfloat162*>(op.lo + o0) = __halves2bfloat162(l0, l1);
+      *reinterpret_cast<__nv_bfloat162*>(op.hi + o1) = __halves2bfloat162(h2, h0);
+      *reinterpret_cast<__nv_bfloat162*>(op.lo + o1) = __halves2bfloat162(l2, l0);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) ws_[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += ws_[k];
+    f.upart[(size_t)v * gridDim.x + blockIdx.x] = make_double2(t, 0.0);
+  }
+}
+
 // Epilogue with NA core states per thread: one thread per (k, n) of vector
 // v = blockIdx.y computes all NA outputs, so A[:, kn] and psi[v][:][kn] are
 // read once; c' and chi are staged in shared memory as FP32.
 // out[c][k][n] = sum_split part + E psi - chi psi + short-range out for NA
 // core states, G of them per thread (NA / G threads per (k, n): more loads in
 // flight for this latency-bound pass); the projectors are read in FP32.
-template <int NA, int G>
+template <int NA, int G, bool FUSED>
 __global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict__ part, int nsplit,
                                                     double2* __restrict__ psi,
                                                     const float2* __restrict__ psi_f, double2* __restrict__ out,
@@ -574,13 +689,18 @@ __global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict_
   // normalised in place (each element by the one thread that owns it)
   const bool lazy = f.operand_ready && f.norm_part;
   double inv = 1.0;
+  bool vec_active = true;   // (fused update) this vector goes on after this step's normalisation
+  double b_i = 0.0;         // (fused update) b_i = |w_i| as this block computed it
+  if (FUSED && !lazy) vec_active = f.active[v] != 0;
   if (lazy) {
     const double s = block_sum_x(f.norm_part + (size_t)v * f.norm_n, f.norm_n);
-    __shared__ double sinv;
+    __shared__ double sinv, sbn;
     if (threadIdx.x == 0) {
       double iv = 0.0;
+      sbn = 0.0;
       if (f.active_rw[v]) {
         const double bn = sqrt(s);
+        sbn = bn;
         const double ai = f.a[(size_t)v * f.a_stride + f.i - 1];
         int st = 0;
         if (!isfinite(bn) || !isfinite(ai)) st = 2;
@@ -599,6 +719,8 @@ __global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict_
     }
     __syncthreads();
     inv = sinv;
+    b_i = sbn;
+    vec_active = inv != 0.0;
   }
   const float finv = (float)inv;
   double dre = 0.0;
@@ -662,6 +784,10 @@ __global__ void __launch_bounds__(256, 4) g2b_final_na(const float2* __restrict_
     }
   }
   if (f.partial) fused_dot_tail(f, dre, 0.0);
+  if constexpr (FUSED) {
+    if (!grid_barrier(f.barrier, gridDim.x * gridDim.y, f.status)) return;
+    fused_update_phase(f, out, psi, (long long)NA * (long long)nkb, vec_active, b_i);
+  }
 }
 
 // out[c][k][n] = sum_split part + E psi - chi psi + short-range out.  Grid
@@ -958,25 +1084,42 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   auto final_grid = [&](int) { return dim3((unsigned)blocks, (unsigned)n_vec); };
   const double2* srp = h->sr_cp;
   const float2* apf = h->a_proj_f;
-  if (h->na == 6) {
-    BSE_PROF(h, BSE_K_PREP,
-             (g2b_final_na<6, 1><<<final_grid(6), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit,
-                                                                       const_cast<double2*>(psi), h->psi_f,
-                                                                       hpsi, h->e_nk, h->chi, apf, srp, h->nk, h->nb,
-                                                                       h->np, nc, f)));
+#define G2B_NA(NA_, FUSED_)                                                                                      \
+  BSE_PROF(h, BSE_K_PREP,                                                                                         \
+           (g2b_final_na<NA_, 1, FUSED_><<<final_grid(NA_), 256, 0, h->stream>>>(                                 \
+               (const float2*)h->part, p.nsplit, const_cast<double2*>(psi), h->psi_f, hpsi, h->e_nk, h->chi, apf, \
+               srp, h->nk, h->nb, h->np, nc, f)))
+  if (h->na == 6 && f.fused_update) {
+    G2B_NA(6, true);
+  } else if (h->na == 6) {
+    G2B_NA(6, false);
+  } else if (h->na == 1 && f.fused_update) {
+    G2B_NA(1, true);
   } else if (h->na == 1) {
-    BSE_PROF(h, BSE_K_PREP,
-             (g2b_final_na<1, 1><<<final_grid(1), 256, 0, h->stream>>>((const float2*)h->part, p.nsplit,
-                                                                       const_cast<double2*>(psi), h->psi_f,
-                                                                       hpsi, h->e_nk, h->chi, apf, srp, h->nk, h->nb,
-                                                                       h->np, nc, f)));
+    G2B_NA(1, false);
   } else {
+    if (f.fused_update) return bse_fail(h, BSE_ERR_UNSUPPORTED, "fused Haydock update needs 1 or 6 core states");
     BSE_PROF(h, BSE_K_PREP,
              g2b_final<<<dim3((unsigned)blocks, (unsigned)n_vec), 256, 0, h->stream>>>(
                  (const float2*)h->part, p.nsplit, psi, hpsi, h->e_nk, h->chi, h->a_proj, h->sr_cp, h->nk, h->nb,
                  h->na, h->np, nc, f));
   }
+#undef G2B_NA
   return bse_cuda_check(h, cudaGetLastError(), "g2b_final launch");
+}
+
+bool bse_tc_fused_update_ok(const bse_handle* h, int n_vec) {
+  const TcState* ts = (const TcState*)h->tmap_host;
+  if (!ts || h->prec != BSE_PREC_SPLIT_BF16 || (h->na != 1 && h->na != 6)) return false;
+  int per_sm = 0;
+  const cudaError_t e = h->na == 6
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g2b_final_na<6, 1, true>, 256, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, g2b_final_na<1, 1, true>, 256, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (long long)per_sm * ts->sms >= (long long)bse_tc_final_blocks(h) * n_vec;
 }
 
 bse_operand_out bse_tc_operand(const bse_handle* h) {

@@ -34,7 +34,7 @@ def test_rixs_tiny_matches_oracle(prec):
     n_steps = 12
     gc = bse.System(core, precision=prec, max_vec=3)
     gv = bse.System(val, precision=prec, max_vec=3)
-    rt = 1e-10 if prec == "fp64" else 1e-6
+    rt = 1e-10 if prec == "fp64" else 1e-5   # tiny grid: the split-bf16 residual floor is near 1e-6
     a, bc, steps, it, rel, st = bse.rixs(gc, gv, b, z, d, n_steps, rtol=rt, restart=30, max_iter=2000)
     assert st == bse.BSE_OK and np.all(rel <= rt) and list(steps) == [n_steps] * 3
     ref = oracle_rixs(core, val, d, b, z, n_steps)
