@@ -376,9 +376,10 @@ typedef enum {
 /* Tile search for the tensor-core form (no counterpart in the paper): times
  * H psi on n_vec (<= max_vec) internal test vectors, reps applications per
  * candidate, for every grid->band split-K factor in {1, 2, 4, 8, 16} (at most
- * one per 64-point K block of the grid) and every pipeline depth in
- * {3, 4, 6, 8} stages that fits shared memory, and keeps the fastest pair for
- * the handle (split_out, stages_out: host, may be NULL).  The choice changes
+ * one per 64-point K block of the grid), every pipeline depth in {3, 4, 6, 8}
+ * stages that fits shared memory and, where bse_set_slabs allows it, 1 or 2
+ * x-slabs, and keeps the fastest choice for the handle (split_out,
+ * stages_out: host, may be NULL; the slab count stays on the handle).  The choice changes
  * only the order of the FP32 partial sums of grid->band.  Other precisions:
  * no-op, outputs 0.  Allocates its test vectors (and a larger partial-sum
  * buffer when needed) and synchronises the handle's stream, so call it
@@ -390,6 +391,22 @@ bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* split_out, int*
  * no-op.  Synchronises the handle's stream; may reallocate the partial-sum
  * buffer. */
 bse_status bse_set_tiles(bse_handle* h, int split_k, int stages);
+
+/* Number of x-slabs of the tensor-core step (no counterpart in the paper):
+ * with slabs = 2 or 4 the real-space grid is cut into that many slabs of
+ * whole 128-point tiles; band->grid runs slab after slab on the handle's
+ * stream, and as soon as a slab's band->grid is done its k->R / x W / R->k
+ * transform and its grid->band contraction run on a second stream, so one
+ * slab's transform overlaps the next slab's contractions; the split-K
+ * partial sums of every slab meet in the grid->band epilogue.  Only the
+ * order of FP32 partial sums changes.  slabs = 1 is the unsplit step.  Needs
+ * the split-bf16 form, a 4^3 or 8^3 k mesh, an even grid and at least one
+ * 128-point tile per slab (BSE_ERR_UNSUPPORTED otherwise; other precisions:
+ * no-op); slabs outside {1, 2, 4}: BSE_ERR_INVALID_ARG.  Synchronises the
+ * handle's stream; may reallocate the partial-sum buffer. */
+bse_status bse_set_slabs(bse_handle* h, int slabs);
+/* The handle's current slab count (0 for NULL). */
+int bse_slabs(const bse_handle* h);
 
 /* Failure-detection aid, no counterpart in the paper: every wait of the
  * tensor-core pipeline (a TMA copy landing, an MMA retiring, an accumulator

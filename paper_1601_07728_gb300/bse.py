@@ -26,7 +26,7 @@ EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", 
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
            "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc",
            "bse_mlp_n_params", "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_params", "bse_mlp_outputs",
-           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0", "bse_set_wait_limit", "bse_rixs", "bse_rixs_emission"]
+           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0", "bse_set_wait_limit", "bse_rixs", "bse_rixs_emission", "bse_set_slabs", "bse_slabs"]
 KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
 
 
@@ -119,6 +119,10 @@ def lib():
     L.bse_set_tiles.restype = ci
     L.bse_set_wait_limit.argtypes = [vp, cd]
     L.bse_set_wait_limit.restype = ci
+    L.bse_set_slabs.argtypes = [vp, ci]
+    L.bse_set_slabs.restype = ci
+    L.bse_slabs.argtypes = [vp]
+    L.bse_slabs.restype = ci
     L.bse_rixs.argtypes = [vp, vp, vp, vp, ci, vp, cd, ci, ci, ci, ci, vp, vp, vp, vp, vp]
     L.bse_rixs.restype = ci
     L.bse_rixs_emission.argtypes = [vp, ci, ci, cll, vp, ci, vp, vp]
@@ -288,6 +292,14 @@ class System:
     def set_tiles(self, split_k=0, stages=0):
         """Fix the tensor-core tile parameters (0 = the set-up rule)."""
         self._check(lib().bse_set_tiles(self.h, int(split_k), int(stages)))
+
+    def set_slabs(self, slabs):
+        """Number of x-slabs of the tensor-core step (1, 2 or 4)."""
+        self._check(lib().bse_set_slabs(self.h, int(slabs)))
+
+    @property
+    def slabs(self):
+        return int(lib().bse_slabs(self.h))
 
     def set_wait_limit(self, seconds):
         """Limit of every wait of the tensor-core pipeline (BSE_ERR_TIMEOUT beyond it)."""

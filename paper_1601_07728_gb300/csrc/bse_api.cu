@@ -25,6 +25,13 @@ bse_status bse_fail(bse_handle* h, bse_status s, const std::string& msg) {
   return s;
 }
 
+void bse_drop_graph(bse_handle* h) {
+  if (h->hay_exec) cudaGraphExecDestroy(h->hay_exec);
+  h->hay_exec = nullptr;
+  h->hay_exec_launches = 0;
+  for (auto& k : h->hay_key) k = 0;
+}
+
 bse_status bse_handle_malloc(bse_handle* h, void** p, size_t bytes, const char* what) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -103,6 +110,7 @@ bse_status stage_out(bse_handle* h, Staged& s, void* p, size_t bytes, const char
 
 void free_handle(bse_handle* h) {
   if (!h) return;
+  bse_drop_graph(h);
   void* ptrs[] = {h->e_nk, h->chi, h->a_proj, h->a_proj_f, h->m_sr, h->jdiag, h->twiddle, h->u, h->w, h->u_hi,
                   h->u_lo, h->ut_hi, h->ut_lo, h->phi, h->sr_c, h->sr_cp, h->sr_part, h->bpsi, h->psi_f, h->bphi,
                   h->part, h->tmap};
@@ -117,6 +125,10 @@ void free_handle(bse_handle* h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
+  for (cudaEvent_t e : h->ev_slab)
+    if (e) cudaEventDestroy(e);
+  if (h->ev_side2) cudaEventDestroy(h->ev_side2);
+  if (h->side2) cudaStreamDestroy(h->side2);
   delete h;
 }
 
@@ -432,6 +444,7 @@ const char* bse_kernel_name(int kind) {
 bse_status bse_profile_enable(bse_handle* h, int enable) {
   if (!h) return BSE_ERR_INVALID_ARG;
   TRY(bse_cuda_check(h, cudaStreamSynchronize(h->stream), "profile sync"));
+  bse_drop_graph(h);   // a cached graph has no profiling events in it
   if (enable && h->ev.empty()) {
     h->ev.resize(2 * 8192);
     h->ev_kind.resize(8192);

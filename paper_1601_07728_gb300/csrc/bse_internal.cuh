@@ -90,6 +90,12 @@ struct bse_handle {
   // side stream for the short-range term (overlaps the band->grid pass)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // x-slabs of the tensor-core step (bse_set_slabs): the k-transform and
+  // grid->band of each slab run on side2 after the slab's band->grid
+  int slabs = 1;
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_slab[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_side2 = nullptr;
   cudaStream_t cur = nullptr;   // stream the next profiled launch goes to
 
   // grow-only device workspace of the Haydock driver (kept between calls)
@@ -112,6 +118,12 @@ struct bse_handle {
   // limit of each wait of the tensor-core pipeline (bse_set_wait_limit)
   unsigned long long tc_wait_ns = 2000000000ull;
 
+  // the last Haydock call's step-loop graph, relaunched when a call repeats it
+  // (same buffers, sizes, tiles and limits); hay_key identifies the call
+  cudaGraphExec_t hay_exec = nullptr;
+  long long hay_exec_launches = 0;   // kernels per launch of the graph
+  unsigned long long hay_key[12] = {0};
+
   // device memory allocated for the handle by bse_setup, and the cap on it
   // (BSE_DEVICE_BYTES_LIMIT in the environment at set-up; 0 = none)
   size_t dev_bytes = 0;
@@ -124,6 +136,9 @@ struct bse_handle {
 // cudaMalloc for a handle's set-up buffers, counted against h->dev_cap
 // (BSE_ERR_OOM beyond it, or when the device is out of memory)
 bse_status bse_handle_malloc(bse_handle* h, void** p, size_t bytes, const char* what);
+
+// drop the cached Haydock graph (tiles, limits or buffers changed)
+void bse_drop_graph(bse_handle* h);
 
 // bracket a launch with profiling events (no-op unless enabled)
 void bse_prof_begin(bse_handle* h, int kind);
@@ -224,13 +239,21 @@ int bse_tc_final_blocks(const bse_handle* h);
 // true if the fused epilogue + Haydock update can run for n_vec vectors (the
 // whole grid of the epilogue is resident at once, so its barrier completes)
 bool bse_tc_fused_update_ok(const bse_handle* h, int n_vec);
+// current tile parameters of the tensor-core form (0, 0 for other forms)
+void bse_tc_tiles(const bse_handle* h, int* split, int* stages);
 bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec);
 bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
                                const bse_dotfuse* fuse, bool wait_side);
+// band->grid, k-transform and grid->band in h->slabs x-slabs (two streams), then the epilogue
+bse_status bse_tc_apply_slabbed(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                                const bse_dotfuse* fuse, bool wait_side);
 bse_status bse_kconv_bf16(bse_handle* h, int n_vec);
 // k-transform x W (k_kconv.cu): in place on phi[k][c][x], or into bf16 hi/lo planes
 bse_status bse_kconv_inplace(bse_handle* h, int n_vec);
-bse_status bse_kconv_split(bse_handle* h, int n_vec, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax);
+bse_status bse_kconv_split(bse_handle* h, int n_vec, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax, int x0, int x1,
+                           cudaStream_t st);
+// true if the k-transform can run on part of the grid (x-slabs)
+bool bse_kconv_takes_slabs(const bse_handle* h);
 bse_status bse_tc_status(bse_handle* h);   // device error word of the tensor-core pipeline
 void bse_tc_free(bse_handle* h);
 

@@ -366,6 +366,7 @@ bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, in
       }
       s = bse_sr_terms(h, psi, n_vec);
       if (s != BSE_OK) return s;
+      if (h->slabs > 1) return bse_tc_apply_slabbed(h, psi, hpsi, n_vec, fuse, h->np > 0);
       s = bse_tc_band_to_grid(h, n_vec);
       if (s != BSE_OK) return s;
       s = bse_kconv_bf16(h, n_vec);

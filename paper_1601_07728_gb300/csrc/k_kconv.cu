@@ -247,7 +247,7 @@ template <int N, bool BF16, int XW>
 __global__ void __launch_bounds__(256) kconv_cubic2(float2* __restrict__ phi, const float* __restrict__ w,
                                                     const double* __restrict__ twiddle,
                                                     __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                                    int nx, int nc, int nnmax) {
+                                                    int nx, int nc, int nnmax, int x0) {
   constexpr int NK = N * N * N, NP = N * N;
   constexpr int XP = XW / 2;                 // x pairs per CTA
   constexpr int NG = 256 / XP;               // pencil groups
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) kconv_cubic2(float2* __restrict__ phi, co
   extern __shared__ __align__(16) unsigned char kc_smem[];
   float4* S = reinterpret_cast<float4*>(kc_smem);   // [NK][XP], each entry (x, x+1)
   const int xp = threadIdx.x & (XP - 1), g = threadIdx.x / XP;
-  const int c = blockIdx.y, x = blockIdx.x * XW + 2 * xp;
+  const int c = blockIdx.y, x = x0 + blockIdx.x * XW + 2 * xp;
   const bool xin = x < nx;                   // Nx even: then x + 1 < Nx as well
   float2 tw[N];
 #pragma unroll
@@ -407,6 +407,110 @@ __global__ void __launch_bounds__(256) kconv_cubic2(float2* __restrict__ phi, co
   }
 }
 
+// kconv_plane8<BF16>: the 8^3 mesh with one shared-memory round trip for the
+// two outer axes.  CTA: one column c and 16 consecutive x, 128 threads.
+//   pass A: thread (x, g) transforms the axis-2 pencils p = g + 8i (i < 8,
+//           p = (m0, m1)) straight from global memory and writes them to the
+//           shared tile S[k][x];
+//   pass P: thread (x, m2) holds the whole (m0, m1) plane of its m2 and x:
+//           forward along axes 1 and 0, times W(x, R)/Nk, inverse along
+//           axes 0 and 1, all in registers, and writes the plane back;
+//   pass E: as pass A, the inverse along axis 2 fused into the store.
+// Shared-memory traffic per point: one write and one read in each half (four
+// accesses, against eight for the pencil-per-pass form).
+template <bool BF16>
+__global__ void __launch_bounds__(128) kconv_plane8(float2* __restrict__ phi, const float* __restrict__ w,
+                                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                                    int nx, int nc, int nnmax, int x0) {
+  constexpr int N = 8, NP = 64, NK = 512, XW = 16;
+  extern __shared__ __align__(16) unsigned char kp_smem[];
+  float2* S = reinterpret_cast<float2*>(kp_smem);   // [NK][XW]
+  const int xl = threadIdx.x & (XW - 1), g = threadIdx.x >> 4;   // g in 0..7
+  const int c = blockIdx.y, x = x0 + blockIdx.x * XW + xl;
+  const bool xin = x < nx;
+  const size_t colstride = (size_t)nc * nx;
+  float2* base = phi + (size_t)c * nx + x;
+  float2 tw[N];   // unused by the radix-8 butterfly; kept for the dftN signature
+#pragma unroll
+  for (int j = 0; j < N; ++j) tw[j] = make_float2(0.f, 0.f);
+  // pass A: pencils p = g + 8i along axis 2 (k = p*8 + j)
+#pragma unroll 2
+  for (int i = 0; i < 8; ++i) {
+    const int p = g + 8 * i;
+    float2 v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = xin ? base[(size_t)(p * N + j) * colstride] : make_float2(0.f, 0.f);
+    dftN<float, N, +1>(v, tw);
+#pragma unroll
+    for (int j = 0; j < N; ++j) S[(p * N + j) * XW + xl] = v[j];
+  }
+  __syncthreads();
+  // pass P: the plane (m0, m1) of m2 = g; k = (m0*8 + m1)*8 + m2
+  {
+    const int m2 = g;
+    float2 pl[N][N];   // [m0][m1]
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int b = 0; b < N; ++b) pl[a][b] = S[((a * N + b) * N + m2) * XW + xl];
+    // forward along axis 1 (m1), then axis 0 (m0)
+#pragma unroll
+    for (int a = 0; a < N; ++a) dftN<float, N, +1>(pl[a], tw);
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      float2 col[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) col[a] = pl[a][b];
+      dftN<float, N, +1>(col, tw);
+      // times W(x, R)/Nk, R = (r0, r1, r2) = (a, b, m2), then the inverse along axis 0
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const float wv = xin ? w[(size_t)((a * N + b) * N + m2) * nx + x] * (1.f / (float)NK) : 0.f;
+        col[a].x *= wv;
+        col[a].y *= wv;
+      }
+      dftN<float, N, -1>(col, tw);
+#pragma unroll
+      for (int a = 0; a < N; ++a) pl[a][b] = col[a];
+    }
+    // inverse along axis 1
+#pragma unroll
+    for (int a = 0; a < N; ++a) dftN<float, N, -1>(pl[a], tw);
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int b = 0; b < N; ++b) S[((a * N + b) * N + m2) * XW + xl] = pl[a][b];
+  }
+  __syncthreads();
+  // pass E: inverse along axis 2 + store
+#pragma unroll 2
+  for (int i = 0; i < 8; ++i) {
+    const int p = g + 8 * i;
+    float2 v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = S[(p * N + j) * XW + xl];
+    dftN<float, N, -1>(v, tw);
+    if (xin) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int k = p * N + j;
+        if constexpr (BF16) {
+          const size_t o = (((size_t)k * ((nx + 63) >> 6) + (x >> 6)) * nnmax + 2 * c) * 64 + (x & 63);
+          __nv_bfloat16 h0, l0, h1, l1;
+          split_bf(v[j].x, h0, l0);
+          split_bf(v[j].y, h1, l1);
+          hi[o] = h0;
+          lo[o] = l0;
+          hi[o + 64] = h1;
+          lo[o + 64] = l1;
+        } else {
+          base[(size_t)k * colstride] = v[j];
+        }
+      }
+    }
+  }
+}
+
 // Generic mesh: one shared-memory pass per axis with explicit sums; CTA owns
 // XC consecutive x of one column c.  S[k][xl].
 template <typename T, int SIGN>
@@ -513,32 +617,53 @@ void launch_cubic(bse_handle* h, dim3 g, typename CT<T>::t* phi, const T* w, __n
 
 template <int N, bool BF16, int XW>
 void launch_cubic2(bse_handle* h, float2* phi, const float* w, __nv_bfloat16* hi, __nv_bfloat16* lo, int nc,
-                   int nnmax) {
+                   int nnmax, int x0, int x1, cudaStream_t st) {
   const size_t smem = (size_t)N * N * N * XW * sizeof(float2);
-  const dim3 g((unsigned)((h->nx + XW - 1) / XW), (unsigned)nc);
+  const dim3 g((unsigned)((x1 - x0 + XW - 1) / XW), (unsigned)nc);
   cudaFuncSetAttribute(kconv_cubic2<N, BF16, XW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   BSE_PROF(h, BSE_K_KCONV,
-           kconv_cubic2<N, BF16, XW><<<g, 256, smem, h->stream>>>(phi, w, h->twiddle, hi, lo, h->nx, nc, nnmax));
+           kconv_cubic2<N, BF16, XW><<<g, 256, smem, st>>>(phi, w, h->twiddle, hi, lo, h->nx, nc, nnmax, x0));
 }
 
+template <bool BF16>
+void launch_plane8(bse_handle* h, float2* phi, const float* w, __nv_bfloat16* hi, __nv_bfloat16* lo, int nc,
+                   int nnmax, int x0, int x1, cudaStream_t st) {
+  const size_t smem = (size_t)512 * 16 * sizeof(float2);
+  const dim3 g((unsigned)((x1 - x0 + 15) / 16), (unsigned)nc);
+  cudaFuncSetAttribute(kconv_plane8<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  BSE_PROF(h, BSE_K_KCONV, kconv_plane8<BF16><<<g, 128, smem, st>>>(phi, w, hi, lo, h->nx, nc, nnmax, x0));
+}
+
+// x range [x0, x1) on stream st: only the pencil and plane forms take a
+// part of the grid (x-slabs of the tensor-core step); the others the whole
 template <typename T, bool BF16>
-bse_status launch(bse_handle* h, int nc, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax) {
+bse_status launch(bse_handle* h, int nc, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax, int x0, int x1,
+                  cudaStream_t st) {
   typedef typename CT<T>::t C;
   C* phi = (C*)h->phi;
   const T* w = (const T*)h->w;
   const dim3 g((unsigned)((h->nx + XC - 1) / XC), (unsigned)nc);
   const int n = h->nk3[0];
   if constexpr (sizeof(T) == sizeof(float)) {
+    // wide passes (more than 128 columns) on the 8^3 mesh: the plane form
+    // (1200 columns of the L2,3 workload: 26.1 vs 28.0 ms per H application);
+    // narrow ones keep the pencil form (6 columns: 59 vs 82 us)
+    if (n == 8 && h->nk3[1] == 8 && h->nk3[2] == 8 && nc > 128) {
+      launch_plane8<BF16>(h, (float2*)phi, (const float*)w, hi, lo, nc, nnmax, x0, x1, st);
+      return bse_cuda_check(h, cudaGetLastError(), "k-transform launch");
+    }
     if (h->nk3[1] == n && h->nk3[2] == n && (n == 4 || n == 8) && h->nx % 2 == 0) {
       // FP32, even Nx: two x per thread, 16 x per CTA (measured against 8 x
       // per CTA at four CTAs per SM on the 8^3 mesh: 59 vs 90 us)
       if (n == 8)
-        launch_cubic2<8, BF16, 16>(h, (float2*)phi, (const float*)w, hi, lo, nc, nnmax);
+        launch_cubic2<8, BF16, 16>(h, (float2*)phi, (const float*)w, hi, lo, nc, nnmax, x0, x1, st);
       else
-        launch_cubic2<4, BF16, 16>(h, (float2*)phi, (const float*)w, hi, lo, nc, nnmax);
+        launch_cubic2<4, BF16, 16>(h, (float2*)phi, (const float*)w, hi, lo, nc, nnmax, x0, x1, st);
       return bse_cuda_check(h, cudaGetLastError(), "k-transform launch");
     }
   }
+  if (x0 != 0 || x1 != h->nx || st != h->stream)
+    return bse_fail(h, BSE_ERR_UNSUPPORTED, "k-transform of part of the grid needs the 4^3 or 8^3 FP32 forms");
   if (h->nk3[1] == n && h->nk3[2] == n && n <= 8) {
 #define KCUBIC(NN)                                                  \
   case NN:                                                          \
@@ -571,11 +696,18 @@ bse_status launch(bse_handle* h, int nc, __nv_bfloat16* hi, __nv_bfloat16* lo, i
 // phi[k][c][x] in place (FP64 / FP32 forms)
 bse_status bse_kconv_inplace(bse_handle* h, int n_vec) {
   const int nc = n_vec * h->na;
-  if (h->prec == BSE_PREC_FP64) return launch<double, false>(h, nc, nullptr, nullptr, 0);
-  return launch<float, false>(h, nc, nullptr, nullptr, 0);
+  if (h->prec == BSE_PREC_FP64) return launch<double, false>(h, nc, nullptr, nullptr, 0, 0, h->nx, h->stream);
+  return launch<float, false>(h, nc, nullptr, nullptr, 0, 0, h->nx, h->stream);
 }
 
-// phi[k][c][x] (FP32) -> bf16 hi/lo planes [k][2c+s][x] with row stride nnmax
-bse_status bse_kconv_split(bse_handle* h, int n_vec, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax) {
-  return launch<float, true>(h, n_vec * h->na, hi, lo, nnmax);
+// phi[k][c][x] (FP32) -> bf16 hi/lo planes [k][2c+s][x] with row stride nnmax,
+// for x in [x0, x1) on stream st
+bse_status bse_kconv_split(bse_handle* h, int n_vec, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax, int x0, int x1,
+                           cudaStream_t st) {
+  return launch<float, true>(h, n_vec * h->na, hi, lo, nnmax, x0, x1, st);
+}
+
+bool bse_kconv_takes_slabs(const bse_handle* h) {
+  const int n = h->nk3[0];
+  return h->prec != BSE_PREC_FP64 && h->nk3[1] == n && h->nk3[2] == n && (n == 4 || n == 8) && h->nx % 2 == 0;
 }

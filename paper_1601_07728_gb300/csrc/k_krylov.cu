@@ -9,6 +9,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <vector>
 
 namespace {
@@ -849,6 +850,26 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   // without a capturable stream it runs eagerly.  Profiling events become
   // event-record nodes of the graph.
   const bool want_graph = allow_graph && h->stream != nullptr && !getenv("BSE_NO_GRAPH");
+  // A call that repeats the previous one (same buffers, sizes and tiles; no
+  // per-call re-orthogonalisation buffers, no profiling events) relaunches
+  // its instantiated graph instead of capturing the loop again.
+  int t_split = 0, t_stages = 0;
+  bse_tc_tiles(h, &t_split, &t_stages);
+  const unsigned long long key[12] = {(unsigned long long)(uintptr_t)b, (unsigned long long)(uintptr_t)a_d,
+                                      (unsigned long long)(uintptr_t)b_d, (unsigned long long)(uintptr_t)steps_d,
+                                      (unsigned long long)(uintptr_t)h->ws, (unsigned long long)n_vec,
+                                      (unsigned long long)n_steps, (unsigned long long)t_split,
+                                      (unsigned long long)t_stages, h->tc_wait_ns,
+                                      (unsigned long long)(uintptr_t)st, 1ull};
+  const bool cacheable = want_graph && !reorth && !h->prof;
+  if (cacheable && h->hay_exec && std::equal(key, key + 12, h->hay_key)) {
+    TRY(bse_cuda_check(h, cudaGraphLaunch(h->hay_exec, st), "haydock graph launch"));
+    h->launches += h->hay_exec_launches;
+    *status_out = status;
+    return bse_cuda_check(h, cudaGetLastError(), "haydock kernels");
+  }
+  bse_drop_graph(h);
+  const long long launches0 = h->launches;
   bool capturing = false;
   if (want_graph) {
     capturing = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -944,8 +965,14 @@ bse_status hay_enqueue(bse_handle* h, const double2* b, int n_vec, int n_steps, 
   cudaGraphExec_t exec = nullptr;
   if (ge == cudaSuccess && loop_status == BSE_OK) ge = cudaGraphInstantiate(&exec, graph, 0);
   if (ge == cudaSuccess && loop_status == BSE_OK) ge = cudaGraphLaunch(exec, st);
-  if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
+  if (ge == cudaSuccess && loop_status == BSE_OK && cacheable) {
+    h->hay_exec = exec;   // kept for a repeat of this call
+    h->hay_exec_launches = h->launches - launches0;
+    std::copy(key, key + 12, h->hay_key);
+    exec = nullptr;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
   if (ge == cudaSuccess && loop_status == BSE_OK) break;
   cudaGetLastError();   // capture refused: run the same launches eagerly
   }

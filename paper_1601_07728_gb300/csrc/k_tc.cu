@@ -154,6 +154,9 @@ struct TcParams {
   int kb_per_split, kb_total;
   int nn;              // MMA N of one tile (multiple of 16, <= 256)
   int ntn;             // N tiles (B rows nt*nn .. nt*nn + nn - 1, two rows per complex column)
+  int mt0;             // first M tile (band->grid over one x-slab)
+  int kb_base;         // first K block and ...
+  int split_base;      // ... first partial-sum slot (grid->band over one x-slab)
   int stages;
   uint32_t tmem_cols;
   float2* out;
@@ -173,10 +176,10 @@ __device__ __forceinline__ Tile decode(const TcParams& p, int t) {
   t /= p.ntn;
   r.split = t % p.nsplit;
   int rest = t / p.nsplit;
-  r.mt = rest % p.mtiles;
+  r.mt = p.mt0 + rest % p.mtiles;
   r.batch = rest / p.mtiles;
-  r.kb0 = r.split * p.kb_per_split;
-  int left = p.kb_total - r.kb0;
+  r.kb0 = p.kb_base + r.split * p.kb_per_split;
+  int left = p.kb_base + p.kb_total - r.kb0;
   r.nkb = left < p.kb_per_split ? left : p.kb_per_split;
   if (r.nkb < 0) r.nkb = 0;
   return r;
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int n = row >> 1;
           if ((lane & 1) == 0 && n < p.nb) {
             // partials [split][k][c][n]
-            float2* o = p.out + ((size_t)tl.split * p.nk + tl.batch) * p.nc * p.nb + n;
+            float2* o = p.out + ((size_t)(p.split_base + tl.split) * p.nk + tl.batch) * p.nc * p.nb + n;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int c = cbase + c16 * 8 + i;
@@ -929,7 +932,7 @@ int pick_stages(int nn, int tuned) {
 }
 
 bse_status launch_gemm(bse_handle* h, TcState* ts, int mode, const CUtensorMap& a_hi, const CUtensorMap& a_lo,
-                       const CUtensorMap& b_hi, const CUtensorMap& b_lo, TcParams p, int kind) {
+                       const CUtensorMap& b_hi, const CUtensorMap& b_lo, TcParams p, int kind, cudaStream_t st) {
   p.stages = pick_stages(p.nn, ts->stages);
   if (p.stages < 2) return bse_fail(h, BSE_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
   uint32_t cols = 32;
@@ -941,7 +944,7 @@ bse_status launch_gemm(bse_handle* h, TcState* ts, int mode, const CUtensorMap& 
   cudaFuncSetAttribute(tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = p.ntiles < ts->sms ? p.ntiles : ts->sms;
   if (grid < 1) return BSE_OK;
-  BSE_PROF(h, kind, tc_gemm<<<grid, TC_THREADS, smem, h->stream>>>(a_hi, a_lo, b_hi, b_lo, p));
+  BSE_PROF(h, kind, tc_gemm<<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p));
   (void)mode;
   return bse_cuda_check(h, cudaGetLastError(), "tc_gemm launch");
 }
@@ -1003,10 +1006,12 @@ bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_d
   const int nc = n_vec * h->na;
   const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
   const size_t total = (size_t)nc * h->nk * h->nb;
-  // two blocks per SM: each block of the lazy-normalisation form first reduces
-  // the update's |w|^2 partials in FP64 (slow pipe), so fewer blocks pay
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)2 * ts->sms);
-  bse_dotfuse f = (fuse && fuse->norm_part) ? *fuse : bse_dotfuse();
+  // with the lazy normalisation each block first reduces the update's |w|^2
+  // partials in FP64 (slow pipe), so two blocks per SM; without it (plain
+  // H psi, GMRES's wide passes) enough blocks to keep loads in flight
+  const bool lazy = fuse && fuse->norm_part;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)(lazy ? 2 : 16) * ts->sms);
+  bse_dotfuse f = lazy ? *fuse : bse_dotfuse();
   if (f.norm_part && n_vec > PREP_MAXV) return bse_fail(h, BSE_ERR_UNSUPPORTED, "lazy normalisation: too many vectors");
   BSE_PROF(h, BSE_K_PREP,
            prep_bpsi<<<blocks, 256, 0, h->stream>>>(const_cast<double2*>(psi), h->bpsi, h->bpsi + nbp, h->psi_f,
@@ -1014,7 +1019,9 @@ bse_status bse_tc_prep(bse_handle* h, const double2* psi, int n_vec, const bse_d
   return bse_cuda_check(h, cudaGetLastError(), "prep_bpsi launch");
 }
 
-bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec) {
+namespace {
+// band->grid over the M tiles [mt_b, mt_e) (x rows mt*128 ..), on stream st
+bse_status b2g_range(bse_handle* h, int n_vec, int mt_b, int mt_e, cudaStream_t st) {
   TcState* ts = (TcState*)h->tmap_host;
   const int nc = n_vec * h->na;
   const int rows = round_up(2 * nc, 16);
@@ -1028,7 +1035,8 @@ bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec) {
     return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
   TcParams p{};
   p.mode = 0;
-  p.mtiles = (h->nx + TC_M - 1) / TC_M;
+  p.mt0 = mt_b;
+  p.mtiles = mt_e - mt_b;
   p.nsplit = 1;
   p.kb_total = (ts->kp + TC_KB - 1) / TC_KB;
   p.kb_per_split = p.kb_total;
@@ -1040,17 +1048,14 @@ bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec) {
   p.nx = h->nx;
   p.nb = h->nb;
   p.nc = nc;
-  return launch_gemm(h, ts, 0, ts->a2_hi, ts->a2_lo, b_hi, b_lo, p, BSE_K_BAND_TO_GRID);
+  return launch_gemm(h, ts, 0, ts->a2_hi, ts->a2_lo, b_hi, b_lo, p, BSE_K_BAND_TO_GRID, st);
 }
 
-bse_status bse_kconv_bf16(bse_handle* h, int n_vec) {
-  TcState* ts = (TcState*)h->tmap_host;
-  const size_t nbf = (size_t)h->nk * ((h->nx + TC_KB - 1) / TC_KB) * ts->nnmax * TC_KB;
-  return bse_kconv_split(h, n_vec, h->bphi, h->bphi + nbf, ts->nnmax);
-}
-
-bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
-                               const bse_dotfuse* fuse, bool wait_side) {
+// grid->band over the K blocks [kb_b, kb_e) (x = kb*64 ..), split into at
+// most `want` parts written to partial slots split_base..; *nsplit_out
+// receives the number of slots written.  On stream st.
+bse_status g2b_range(bse_handle* h, int n_vec, int kb_b, int kb_e, int split_base, int want, int* nsplit_out,
+                     cudaStream_t st) {
   TcState* ts = (TcState*)h->tmap_host;
   const int nc = n_vec * h->na;
   const int rows = round_up(2 * nc, 16);
@@ -1064,10 +1069,13 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   TcParams p{};
   p.mode = 1;
   p.mtiles = (2 * h->nb + TC_M - 1) / TC_M;
-  p.kb_total = (h->nx + TC_KB - 1) / TC_KB;
-  p.nsplit = ts->smax < p.kb_total ? ts->smax : p.kb_total;
+  p.kb_base = kb_b;
+  p.kb_total = kb_e - kb_b;
+  p.nsplit = want < p.kb_total ? want : p.kb_total;
+  if (p.nsplit < 1) p.nsplit = 1;
   p.kb_per_split = (p.kb_total + p.nsplit - 1) / p.nsplit;
   p.nsplit = (p.kb_total + p.kb_per_split - 1) / p.kb_per_split;   // no empty split
+  p.split_base = split_base;
   p.ntn = (rows + nn - 1) / nn;
   p.ntiles = h->nk * p.mtiles * p.nsplit * p.ntn;
   p.nn = nn;
@@ -1076,8 +1084,33 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   p.nx = h->nx;
   p.nb = h->nb;
   p.nc = nc;
-  bse_status s = launch_gemm(h, ts, 1, ts->a6_hi, ts->a6_lo, b_hi, b_lo, p, BSE_K_GRID_TO_BAND);
-  if (s != BSE_OK) return s;
+  *nsplit_out = p.nsplit;
+  return launch_gemm(h, ts, 1, ts->a6_hi, ts->a6_lo, b_hi, b_lo, p, BSE_K_GRID_TO_BAND, st);
+}
+
+}  // namespace
+
+bse_status bse_tc_band_to_grid(bse_handle* h, int n_vec) {
+  TcState* ts = (TcState*)h->tmap_host;
+  (void)ts;
+  return b2g_range(h, n_vec, 0, (h->nx + TC_M - 1) / TC_M, h->stream);
+}
+
+bse_status bse_kconv_bf16(bse_handle* h, int n_vec) {
+  TcState* ts = (TcState*)h->tmap_host;
+  const size_t nbf = (size_t)h->nk * ((h->nx + TC_KB - 1) / TC_KB) * ts->nnmax * TC_KB;
+  return bse_kconv_split(h, n_vec, h->bphi, h->bphi + nbf, ts->nnmax, 0, h->nx, h->stream);
+}
+
+namespace {
+// grid->band epilogue: sums the nsplit split-K partials, adds E psi - chi psi
+// and the short-range projection out (and the Haydock hooks of `fuse`)
+bse_status g2b_epilogue(bse_handle* h, const double2* psi, double2* hpsi, int n_vec, const bse_dotfuse* fuse,
+                        bool wait_side, int nsplit) {
+  const int nc = n_vec * h->na;
+  struct {
+    int nsplit;
+  } p{nsplit};
   if (wait_side) cudaStreamWaitEvent(h->stream, h->ev_join, 0);   // short-range c' ready
   const int blocks = bse_tc_final_blocks(h);
   bse_dotfuse f = fuse ? *fuse : bse_dotfuse();
@@ -1106,6 +1139,60 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   }
 #undef G2B_NA
   return bse_cuda_check(h, cudaGetLastError(), "g2b_final launch");
+}
+}  // namespace
+
+bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                               const bse_dotfuse* fuse, bool wait_side) {
+  TcState* ts = (TcState*)h->tmap_host;
+  int ns = 1;
+  bse_status s = g2b_range(h, n_vec, 0, (h->nx + TC_KB - 1) / TC_KB, 0, ts->smax, &ns, h->stream);
+  if (s != BSE_OK) return s;
+  return g2b_epilogue(h, psi, hpsi, n_vec, fuse, wait_side, ns);
+}
+
+// The step in x-slabs: band->grid of every slab on the handle's stream, and
+// for each slab, once its band->grid is done, the k-transform and grid->band
+// of that slab on a second stream -- so a slab's k-transform runs beside the
+// next slab's contractions -- then the epilogue over every slab's partials.
+bse_status bse_tc_apply_slabbed(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                                const bse_dotfuse* fuse, bool wait_side) {
+  TcState* ts = (TcState*)h->tmap_host;
+  const int S = h->slabs;
+  const int mt = (h->nx + TC_M - 1) / TC_M;
+  const int kbt = (h->nx + TC_KB - 1) / TC_KB;
+  const size_t nbf = (size_t)h->nk * kbt * ts->nnmax * TC_KB;
+  const int sps = ts->smax / S > 1 ? ts->smax / S : 1;   // split-K parts per slab
+  bse_status s = BSE_OK;
+  for (int i = 0; i < S && s == BSE_OK; ++i) {
+    s = b2g_range(h, n_vec, mt * i / S, mt * (i + 1) / S, h->stream);
+    cudaEventRecord(h->ev_slab[i], h->stream);
+  }
+  if (s != BSE_OK) return s;
+  int base = 0;
+  h->cur = h->side2;
+  for (int i = 0; i < S && s == BSE_OK; ++i) {
+    const int m0 = mt * i / S, m1 = mt * (i + 1) / S;
+    const int x0 = m0 * TC_M, x1 = m1 * TC_M < h->nx ? m1 * TC_M : h->nx;
+    cudaStreamWaitEvent(h->side2, h->ev_slab[i], 0);
+    s = bse_kconv_split(h, n_vec, h->bphi, h->bphi + nbf, ts->nnmax, x0, x1, h->side2);
+    if (s != BSE_OK) break;
+    int ns = 0;
+    const int kb1 = (x1 + TC_KB - 1) / TC_KB;
+    s = g2b_range(h, n_vec, x0 / TC_KB, kb1, base, sps, &ns, h->side2);
+    base += ns;
+  }
+  h->cur = nullptr;
+  cudaEventRecord(h->ev_side2, h->side2);
+  cudaStreamWaitEvent(h->stream, h->ev_side2, 0);
+  if (s != BSE_OK) return s;
+  return g2b_epilogue(h, psi, hpsi, n_vec, fuse, wait_side, base);
+}
+
+void bse_tc_tiles(const bse_handle* h, int* split, int* stages) {
+  const TcState* ts = (const TcState*)h->tmap_host;
+  *split = ts ? ts->smax : 0;
+  *stages = ts ? ts->stages : 0;
 }
 
 bool bse_tc_fused_update_ok(const bse_handle* h, int n_vec) {
@@ -1154,6 +1241,64 @@ int bse_tc_final_blocks(const bse_handle* h) {
   return (int)bk;
 }
 
+namespace {
+// partial-sum buffer for `need` split-K slots (outside any stream capture)
+bse_status ensure_part_cap(bse_handle* h, TcState* ts, int need) {
+  if (need <= ts->part_cap) return BSE_OK;
+  float2* np = nullptr;
+  if (cudaMalloc((void**)&np, (size_t)need * h->nk * h->nb * h->na * h->max_vec * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    return bse_fail(h, BSE_ERR_OOM, "partial-sum buffer");
+  }
+  cudaFree(h->part);
+  h->part = (float*)np;
+  ts->part_cap = need;
+  return BSE_OK;
+}
+
+// slab count 1, 2 or 4 (streams and events created on first use)
+bse_status apply_slabs(bse_handle* h, TcState* ts, int slabs) {
+  if (slabs > 1) {
+    if (!h->side2) {
+      if (cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_side2, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return bse_fail(h, BSE_ERR_CUDA, "slab stream creation failed");
+      }
+      for (auto& e : h->ev_slab)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          return bse_fail(h, BSE_ERR_CUDA, "slab event creation failed");
+        }
+    }
+    const int sps = ts->smax / slabs > 1 ? ts->smax / slabs : 1;
+    const bse_status s = ensure_part_cap(h, ts, slabs * sps);
+    if (s != BSE_OK) return s;
+  }
+  h->slabs = slabs;
+  bse_drop_graph(h);
+  return BSE_OK;
+}
+
+bool slabs_allowed(const bse_handle* h, int slabs) {
+  return slabs == 1 || (bse_kconv_takes_slabs(h) && (h->nx + TC_M - 1) / TC_M >= slabs);
+}
+}  // namespace
+
+// Number of x-slabs of the tensor-core step (see bse_set_slabs in bse.h).
+extern "C" bse_status bse_set_slabs(bse_handle* h, int slabs) {
+  if (!h) return BSE_ERR_INVALID_ARG;
+  if (slabs != 1 && slabs != 2 && slabs != 4) return bse_fail(h, BSE_ERR_INVALID_ARG, "set_slabs: slabs must be 1, 2 or 4");
+  if (h->prec != BSE_PREC_SPLIT_BF16 || !h->tmap_host) return BSE_OK;
+  if (!slabs_allowed(h, slabs))
+    return bse_fail(h, BSE_ERR_UNSUPPORTED, "set_slabs: needs a 4^3 or 8^3 k mesh, an even grid and one 128-row tile per slab");
+  const bse_status ss = bse_cuda_check(h, cudaStreamSynchronize(h->stream), "set_slabs sync");
+  if (ss != BSE_OK) return ss;
+  return apply_slabs(h, (TcState*)h->tmap_host, slabs);
+}
+
+extern "C" int bse_slabs(const bse_handle* h) { return h ? h->slabs : 0; }
+
 // Limit of every pipeline wait of the tensor-core kernel (see bse_set_wait_limit in bse.h).
 extern "C" bse_status bse_set_wait_limit(bse_handle* h, double seconds) {
   if (!h) return BSE_ERR_INVALID_ARG;
@@ -1162,6 +1307,7 @@ extern "C" bse_status bse_set_wait_limit(bse_handle* h, double seconds) {
   const bse_status ss = bse_cuda_check(h, cudaStreamSynchronize(h->stream), "set_wait_limit sync");
   if (ss != BSE_OK) return ss;
   h->tc_wait_ns = (unsigned long long)(seconds * 1e9);
+  bse_drop_graph(h);
   return BSE_OK;
 }
 
@@ -1196,7 +1342,8 @@ extern "C" bse_status bse_set_tiles(bse_handle* h, int split_k, int stages) {
   }
   ts->smax = split_k;
   ts->stages = stages;
-  return BSE_OK;
+  bse_drop_graph(h);
+  return apply_slabs(h, ts, h->slabs);   // the slabs' partial slots for the new split
 }
 
 // Timed search over the tensor-core tile parameters of one handle (see
@@ -1247,14 +1394,21 @@ extern "C" bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* spli
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int keep_split = ts->smax, keep_stages = ts->stages;
-  int best_split = keep_split, best_stages = keep_stages;
+  const int keep_split = ts->smax, keep_stages = ts->stages, keep_slabs = h->slabs;
+  int best_split = keep_split, best_stages = keep_stages, best_slabs = keep_slabs;
   float best = 3.4e38f;
   bse_status s = BSE_OK;
+  std::vector<int> slab_set;
+  for (int sl : {1, 2})
+    if (slabs_allowed(h, sl)) slab_set.push_back(sl);
+  for (int sl : slab_set)
   for (int sp : splits) {
+    if (s != BSE_OK) break;
     for (int sg : stages) {
       ts->smax = sp;
       ts->stages = sg;
+      s = apply_slabs(h, ts, sl);
+      if (s != BSE_OK) break;
       s = bse_apply_device(h, psi, hpsi, n_vec);   // warm-up
       cudaEventRecord(e0, st);
       for (int r = 0; r < reps && s == BSE_OK; ++r) s = bse_apply_device(h, psi, hpsi, n_vec);
@@ -1267,6 +1421,7 @@ extern "C" bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* spli
         best = ms;
         best_split = sp;
         best_stages = sg;
+        best_slabs = sl;
       }
     }
     if (s != BSE_OK) break;
@@ -1279,10 +1434,13 @@ extern "C" bse_status bse_autotune(bse_handle* h, int n_vec, int reps, int* spli
   if (s != BSE_OK) {
     ts->smax = keep_split;
     ts->stages = keep_stages;
+    apply_slabs(h, ts, keep_slabs);
     return s;
   }
   ts->smax = best_split;
   ts->stages = best_stages;
+  s = apply_slabs(h, ts, best_slabs);
+  if (s != BSE_OK) return s;
   if (split_out) *split_out = best_split;
   if (stages_out) *stages_out = best_stages;
   return BSE_OK;

@@ -308,6 +308,102 @@ def test_haydock_single_vector_fused_update_breakdown():
     close("fused_update/b31", bc[0], bo, (1e-10, 1e-10))
 
 
+def test_haydock_repeat_relaunches_cached_graph():
+    """A Haydock call that repeats the previous one (same device buffers,
+    sizes and tiles) relaunches the instantiated step-loop graph: the same
+    bits, the same number of kernels counted; new tiles drop the graph and the
+    rebuilt one still matches the oracle."""
+    torch = pytest.importorskip("torch")
+    s = S.tiny_system(48, n_alpha=6, nk=(2, 2, 2), n_bands=20, nx=(8, 4, 4), n_proj=3)
+    b = torch.from_numpy(S.make_start_vectors(s, 1, seed=4)[0]).cuda()
+    stream = torch.cuda.Stream()
+    sysg = bse.System(s, precision="split_bf16", max_vec=1, stream=stream.cuda_stream)
+    a = torch.zeros((1, 15), dtype=torch.float64, device="cuda")
+    bc = torch.zeros((1, 16), dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = []
+    for _ in range(3):
+        l0 = sysg.launches
+        sysg.haydock(b, 15, a=a, bcoef=bc, steps=st)
+        torch.cuda.synchronize()
+        out.append((a.cpu().numpy().copy(), bc.cpu().numpy().copy(), sysg.launches - l0))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[1][0], out[2][0])
+    assert np.array_equal(out[0][1], out[2][1])
+    assert out[0][2] == out[1][2] == out[2][2] > 15
+    ao, bo, _, _ = O.haydock(lambda x: O.apply_h(s, x), b.cpu().numpy(), 15)
+    sysg.set_tiles(1, 3)
+    sysg.haydock(b, 15, a=a, bcoef=bc, steps=st)
+    torch.cuda.synchronize()
+    close("graph_cache/a_after_tiles", a.cpu().numpy()[0], ao, (2e-5, 5e-5))
+    close("graph_cache/b_after_tiles", bc.cpu().numpy()[0], bo, (2e-5, 5e-5))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_wide_pass_on_8cubed_mesh(prec):
+    """More than 128 columns on the 8^3 k mesh: the plane form of the
+    k-transform (each thread holds one (m0, m1) plane), against the oracle."""
+    s = S.tiny_system(66, n_alpha=6, nk=(8, 8, 8), n_bands=6, nx=(4, 3, 2), n_proj=2)
+    sysg = bse.System(s, precision=prec, max_vec=23)
+    psi = S.complex_normal(np.random.default_rng(66), (23, s.dim))
+    out = sysg.apply_h(psi)
+    ref = O.apply_h(s, psi)
+    close("wide8/apply_h/%s" % prec, out, ref, prec)
+    for v in (0, 11, 22):
+        close("wide8/apply_h/%s/vec%d" % (prec, v), out[v], ref[v], prec)
+
+
+@pytest.mark.parametrize("kw,slabs", [
+    (dict(seed=91, n_alpha=6, nk=(4, 4, 4), n_bands=24, nx=(8, 8, 8), n_proj=3), 2),
+    (dict(seed=91, n_alpha=6, nk=(4, 4, 4), n_bands=24, nx=(8, 8, 8), n_proj=3), 4),
+    (dict(seed=92, n_alpha=1, nk=(8, 8, 8), n_bands=10, nx=(10, 10, 6), n_proj=0), 2),   # 600 points: ragged last slab
+    (dict(seed=93, n_alpha=6, nk=(8, 8, 8), n_bands=6, nx=(8, 8, 4), n_proj=2), 2),
+])
+def test_x_slabs_match_oracle(kw, slabs):
+    """The step in x-slabs (band->grid per slab on one stream, each slab's
+    k-transform and grid->band on a second stream, partials summed by the
+    epilogue) equals the oracle, for one and for two vectors."""
+    s = S.tiny_system(**kw)
+    sysg = bse.System(s, precision="split_bf16", max_vec=2)
+    sysg.set_slabs(slabs)
+    assert sysg.slabs == slabs
+    psi = S.complex_normal(np.random.default_rng(kw["seed"]), (2, s.dim))
+    out = sysg.apply_h(psi)
+    ref = O.apply_h(s, psi)
+    for v in range(2):
+        close("slabs%d/apply_h/seed%d/v%d" % (slabs, kw["seed"], v), out[v], ref[v], "split_bf16")
+
+
+def test_x_slabs_haydock_and_wide_pass():
+    """Two slabs inside the captured Haydock loop (fused epilogue/update) and
+    in a 138-column pass: both against the oracle."""
+    torch = pytest.importorskip("torch")
+    s = S.tiny_system(94, n_alpha=6, nk=(8, 8, 8), n_bands=6, nx=(8, 8, 4), n_proj=2)
+    b = S.make_start_vectors(s, 1, seed=2)[0]
+    stream = torch.cuda.Stream()
+    sysg = bse.System(s, precision="split_bf16", max_vec=1, stream=stream.cuda_stream)
+    sysg.set_slabs(2)
+    a, bc, steps, st = sysg.haydock(b, 15)
+    ao, bo, _, _ = O.haydock(lambda x: O.apply_h(s, x), b, 15)
+    assert st == bse.BSE_OK and steps[0] == 15
+    close("slabs2/haydock_a", a[0], ao, (2e-5, 5e-5))
+    close("slabs2/haydock_b", bc[0], bo, (2e-5, 5e-5))
+    wide = bse.System(s, precision="split_bf16", max_vec=23)
+    wide.set_slabs(2)
+    psi = S.complex_normal(np.random.default_rng(94), (23, s.dim))
+    close("slabs2/wide", wide.apply_h(psi), O.apply_h(s, psi), "split_bf16")
+
+
+def test_x_slabs_refused_where_unsupported():
+    s = S.tiny_system(95, n_alpha=2, nk=(2, 3, 2), n_bands=8, nx=(4, 4, 4), n_proj=1)
+    sysg = bse.System(s, precision="split_bf16")
+    with pytest.raises(bse.BSEError) as e:
+        sysg.set_slabs(2)     # 2x3x2 mesh: the k-transform cannot take part of the grid
+    assert e.value.status == bse.BSE_ERR_UNSUPPORTED
+    with pytest.raises(bse.BSEError) as e:
+        sysg.set_slabs(3)
+    assert e.value.status == bse.BSE_ERR_INVALID_ARG
+
+
 def test_apply_h_device_pointers():
     torch = pytest.importorskip("torch")
     s = S.tiny_system(30, n_alpha=6, nk=(2, 2, 2), n_bands=12, nx=(6, 6, 6), n_proj=4)
