@@ -528,6 +528,21 @@ def main():
         # measured ones (residual probes of plain GMRES(30), 10-step minimal-residual loss)
         net = bse.MLP(S.mlp_init(0))
         bse.attach_mlp(sys_g, net)
+        # network inference alone: features + three dense layers (FP16 weights,
+        # FP32 accumulate) for every row at one shift, device output
+        net.outputs(sys_g, 10.0, 0.5)          # grows the network's row buffers once
+        sys_g.profile(True)
+        for _ in range(5):
+            net.outputs(sys_g, 10.0, 0.5)
+        n_inf, t_inf = sys_g.profile_read()["prep"]   # the feature and three dense-layer kernels
+        sys_g.profile(False)
+        inf_ms = t_inf / 5
+        inf_fl = 2.0 * n * (12 * 128 + 128 * 128 + 128 * 34)
+        gm["mlp_inference"] = {"ms_per_shift": inf_ms, "kernel_launches": n_inf // 5, "rows": n,
+                               "tflops": inf_fl / (inf_ms / 1e3) / 1e12,
+                               "gflop_per_shift": inf_fl / 1e9,
+                               "note": "features + 12-128-128-34 network for every row at one shift (SIMT, FP16 "
+                                       "weights, FP32 accumulate); a 200-shift build is 200 of these"}
         gm["mlp_prior"] = leg(sys_g, "mlp", zs, xg)
         if args.train_omega > 0:
             step = (zs[1].real - zs[0].real) if n_om > 1 else 1.0
