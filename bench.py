@@ -756,7 +756,11 @@ def main():
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "desc": workload_desc(args.workload), "precision": args.precision,
                        "recursion": "f64 Haydock, no re-orthogonalisation", "n_vec": 1, "dim": n,
-                       "l2": "inputs larger than L2 (u_nk 1.07 GB), no flush", "parallelism": "replicas",
+                       "l2": ("inputs larger than L2 (u_nk %.2f GB), no flush" % (u_bytes(s, args.precision) / 1e9)
+                              if u_bytes(s, args.precision) > 129e6 else
+                              "u_nk %.0f MB fits in L2: steps reuse it (a small case, not a headline)"
+                              % (u_bytes(s, args.precision) / 1e6)),
+                       "parallelism": "replicas",
                        "tiles": {"grid_to_band_split_k": tiles[0], "pipeline_stages": tiles[1],
                                  "x_slabs": sysg.slabs, "chosen_by": tiles_by}},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -16,6 +16,20 @@ namespace {
 
 constexpr int RB = 256;      // threads per reduction block
 constexpr int NBLK = 296;    // partial-sum blocks per vector (2 x 148)
+
+// Blocks per vector of a norm over nv vectors of length N: about 4096
+// elements per block, but at least ~608 blocks in all (four per SM of 152),
+// at most NBLK -- so that many short vectors (GMRES over many shifts) do not
+// pay a block reduction per few dozen elements.
+inline int norm_blocks(long long N, int nv) {
+  long long nb = (N + 4095) / 4096;
+  const long long fill = (608 + nv - 1) / nv;
+  if (nb < fill) nb = fill;
+  if (nb > NBLK) nb = NBLK;
+  const long long cap = (N + 255) / 256;
+  if (nb > cap) nb = cap;
+  return (int)(nb < 1 ? 1 : nb);
+}
 constexpr int UBLK = 296;    // blocks per vector of the Haydock update (its |w|^2 partials are reduced again by every block of the next operand pass)
 
 enum { ST_BREAKDOWN = 1, ST_NAN = 2, ST_TIMEOUT = BSE_ST_TIMEOUT };
@@ -334,8 +348,9 @@ bse_status cgs_dgks(bse_handle* h, const double2* basis, long long bstride, doub
   BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(GS_BLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask));
   BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, GS_BLK, coef, coef_stride, hacc, hacc_stride));
   BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask));
-  BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, nv), RB, 0, st>>>(w, N, nullptr, 0, N, partial));
-  BSE_PROF(h, BSE_K_RECURSION, gs_dgks_mask<<<nv, RB, 0, st>>>(partial, NBLK, coef, coef_stride, nj, mask, mask2));
+  const int nbn = norm_blocks(N, nv);
+  BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(nbn, nv), RB, 0, st>>>(w, N, nullptr, 0, N, partial));
+  BSE_PROF(h, BSE_K_RECURSION, gs_dgks_mask<<<nv, RB, 0, st>>>(partial, nbn, coef, coef_stride, nj, mask, mask2));
   BSE_PROF(h, BSE_K_RECURSION, gs_dot_multi<<<dim3(GS_BLK, nv), RB, 0, st>>>(basis, bstride, w, N, nj, partial, mask2));
   BSE_PROF(h, BSE_K_RECURSION, gs_dot_finalize<<<dim3(nj, nv), RB, 0, st>>>(partial, GS_BLK, coef, coef_stride, hacc, hacc_stride));
   BSE_PROF(h, BSE_K_RECURSION, gs_subtract<<<ew_grid(N, nv), 256, 0, st>>>(basis, bstride, w, N, coef, coef_stride, nj, mask2));
@@ -1135,6 +1150,7 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
     bnorm = sqrt(bnorm);
   }
   if (!(bnorm > 0) || !isfinite(bnorm)) return bse_fail(h, BSE_ERR_INVALID_ARG, "b must be nonzero and finite");
+  const int nbn = norm_blocks(N, n_z);   // blocks per system of the residual and Arnoldi norms
   const bool x0 = (precond & BSE_GMRES_X0) != 0;   // x holds the initial guess
   if (!x0) cudaMemsetAsync(x, 0, (size_t)n_z * N * sizeof(double2), st);
   cudaMemsetAsync(iters_d, 0, n_z * sizeof(int), st);
@@ -1145,8 +1161,8 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
     const bool zero_x = cycle == 0 && !x0;
     if (!zero_x) TRY(apply_chunked(h, x, W, n_z));
     BSE_PROF(h, BSE_K_RECURSION, gm_residual<<<eg, 256, 0, st>>>(b, W, x, z, V, vstride, N, zero_x));
-    BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_z), RB, 0, st>>>(V, vstride, nullptr, 0, N, partial));
-    BSE_PROF(h, BSE_K_RECURSION, gm_beta<<<n_z, RB, 0, st>>>(partial, NBLK, bnorm, rtol, max_iter, iters_d, beta, rel_d, active, g, m));
+    BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(nbn, n_z), RB, 0, st>>>(V, vstride, nullptr, 0, N, partial));
+    BSE_PROF(h, BSE_K_RECURSION, gm_beta<<<n_z, RB, 0, st>>>(partial, nbn, bnorm, rtol, max_iter, iters_d, beta, rel_d, active, g, m));
     TRY(bse_cuda_check(h, cudaMemcpyAsync(hact.data(), active, n_z * sizeof(int), cudaMemcpyDeviceToHost, st), "active copy"));
     TRY(bse_cuda_check(h, cudaStreamSynchronize(st), "gmres sync"));
     int nact = 0;
@@ -1175,8 +1191,8 @@ bse_status bse_gmres_device(bse_handle* h, const double2* b, const double2* z, i
       // Arnoldi: classical Gram-Schmidt, repeated where the DGKS test asks for it
       TRY(cgs_dgks(h, V, vstride, W, n_z, j + 1, partial, coef, m + 1, Hs + (size_t)j * (m + 1),
                    (m + 1) * m, mask, mask2));
-      BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(NBLK, n_z), RB, 0, st>>>(W, N, nullptr, 0, N, partial));
-      BSE_PROF(h, BSE_K_RECURSION, gm_givens<<<n_z, RB, 0, st>>>(partial, NBLK, Hs, cs, sn, g, hnorm, m, j, bnorm, rtol, max_iter,
+      BSE_PROF(h, BSE_K_RECURSION, dot_partial_s<<<dim3(nbn, n_z), RB, 0, st>>>(W, N, nullptr, 0, N, partial));
+      BSE_PROF(h, BSE_K_RECURSION, gm_givens<<<n_z, RB, 0, st>>>(partial, nbn, Hs, cs, sn, g, hnorm, m, j, bnorm, rtol, max_iter,
                                    active, iters_d, jdone, est));
       if (j + 1 < m) {
         BSE_PROF(h, BSE_K_RECURSION, gm_next<<<eg, 256, 0, st>>>(W, N, V + (size_t)(j + 1) * N, vstride, N, hnorm, active));
