@@ -77,6 +77,8 @@ def parse():
                    help="captured Haydock steps of the plain FP64 form on the same workload (0 = skip)")
     p.add_argument("--supercell-steps", type=int, default=20,
                    help="timed Haydock steps on the 48^3-grid supercell workload (0 = skip)")
+    p.add_argument("--no-one-pass", action="store_true",
+                   help="skip the leg that times the one-pass schedule (bse_set_schedule one_pass)")
     p.add_argument("--sites", type=int, default=8,
                    help="sites of the many-site workload run in one batched launch of 200 steps (0 = skip)")
     return p.parse_args()
@@ -488,6 +490,46 @@ def main():
         sys3.close()
         del b3
 
+    # the one-pass schedule (one persistent kernel per H psi, u_nk streamed from
+    # HBM once when the slabs between its two reads stay in L2): the headline's
+    # workload, start vector and step count, timed the same way
+    onep = None
+    if not args.no_one_pass and args.precision == "split_bf16":
+        sys1 = bse.System(s, precision=args.precision, max_vec=1, stream=stream.cuda_stream)
+        try:
+            sys1.set_schedule("one_pass")
+        except bse.BSEError as ex:
+            onep = {"unavailable": str(ex)}
+        else:
+            ms1, done1, _, _, _ = timed_haydock(sys1, db, K, stream)
+            ms1 = max_over_ranks(ms1, dist)
+            sys1.profile(True)
+            sys1.haydock(db, kp, a=ap, bcoef=bp, steps=st_d)
+            torch.cuda.synchronize()
+            n1, t1 = sys1.profile_read()["one_pass"]
+            sys1.profile(False)
+            ab = algorithmic_bytes(s, args.precision)
+            u1 = u_bytes(s, args.precision)
+            # one read of u_nk plus everything else the three two-pass kernels move
+            alg1 = ab["band_to_grid"] + ab["kconv"] + ab["grid_to_band"] - u1
+            k_ms = t1 / max(n1, 1)
+            pk, _ = peaks()
+            onep = {"matvecs_per_s": job_rate(done1, ms1 / 1e3, world), "ms_per_step": ms1 / K, "steps": K,
+                    "lag": 2, "stages": 5, "kernel_ms": k_ms, "kernel_launches": n1,
+                    "alg_bytes_per_launch": alg1, "achieved_gbs": alg1 / (k_ms / 1e3) / 1e9,
+                    "frac_of_hbm_peak": alg1 / (k_ms / 1e3) / 1e9 / pk,
+                    "two_read_bytes_frac": (alg1 + u1) / (k_ms / 1e3) / 1e9 / pk,
+                    "headline_over_one_pass": value / job_rate(done1, ms1 / 1e3, world),
+                    "note": "frac_of_hbm_peak counts u_nk once; two_read_bytes_frac counts the bytes of the "
+                            "two-pass step (u_nk twice), so it can exceed 1"}
+            try:
+                with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+                    onep["dram_bytes_per_launch"] = json.load(f).get("%s/%s/one_pass" % (args.workload,
+                                                                                       args.precision))
+            except Exception:
+                pass
+        sys1.close()
+
     # GMRES: (H - omega - i Gamma) x = b for n_omega shifts, all advanced together
     gm = None
     if args.gmres_omega > 0:
@@ -774,6 +816,7 @@ def main():
             "spectrum": spec,
             "fp64_form": fp64_form,
             "polarisations": pol,
+            "one_pass": onep,
             "supercell": sc,
             "sites": sites,
             "gmres": gm,

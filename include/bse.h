@@ -363,14 +363,15 @@ long long bse_launch_count(const bse_handle* h);
 
 /* Kernel classes timed by the profiling hook below. */
 typedef enum {
-  BSE_K_BAND_TO_GRID = 0,   /* Algorithm 1, first line (band -> grid contraction)     */
-  BSE_K_KCONV = 1,          /* Algorithm 1, lines 3-5 (k->R, x W, R->k)                */
-  BSE_K_GRID_TO_BAND = 2,   /* Algorithm 1, last line + diagonal/spin-orbit/short range */
+  BSE_K_BAND_TO_GRID = 0,   /* Algorithm 1, band -> grid contraction                   */
+  BSE_K_KCONV = 1,          /* Algorithm 1, k->R sum, x W(x,R), R->k sum               */
+  BSE_K_GRID_TO_BAND = 2,   /* Algorithm 1, grid -> band + diagonal/spin-orbit/short range */
   BSE_K_SR_IN = 3,          /* Sec. 3.2.2 projection onto the local basis              */
   BSE_K_SR_COUPLE = 4,      /* Sec. 3.2.2 multiplet coupling c' = M c                  */
   BSE_K_PREP = 5,           /* operand preparation for the tensor-core form            */
   BSE_K_RECURSION = 6,      /* Haydock / GMRES vector kernels (Eq. 9)                  */
-  BSE_K_COUNT = 7
+  BSE_K_ONE_PASS = 7,       /* Algorithm 1: both contractions and the k sums, one pass  */
+  BSE_K_COUNT = 8
 } bse_kernel_kind;
 
 /* Tile search for the tensor-core form (no counterpart in the paper): times
@@ -407,6 +408,40 @@ bse_status bse_set_tiles(bse_handle* h, int split_k, int stages);
 bse_status bse_set_slabs(bse_handle* h, int slabs);
 /* The handle's current slab count (0 for NULL). */
 int bse_slabs(const bse_handle* h);
+
+/* Schedule of the split-bf16 H psi step over U = e^{ik.x} u_nk(x) (Algorithm 1,
+ * Sec. 3.2.1; the schedule is this library's, the paper distributes the same
+ * sums over MPI ranks):
+ *   BSE_SCHED_TWO_PASS (default): band->grid reads U row-major ([k][x][n]),
+ *     grid->band reads a K-tiled transposed copy ([k][x/64][n][64]); U
+ *     streams from HBM once per contraction;
+ *   BSE_SCHED_TWO_PASS_ROWMAJOR: as above, but grid->band reads the row-major
+ *     U as an MN-major tensor-core operand (the transposed copy unused);
+ *   BSE_SCHED_ONE_PASS: one persistent kernel walks the grid in slabs of 128
+ *     points; per slab it runs band->grid for every k, the k->R sum x W(x,R)
+ *     R->k sum of the slab's points, and grid->band for every k reading the
+ *     slab's U again while it is still in L2 -- so U streams from HBM once
+ *     per H psi.  Its CTAs wait on one another (per-slab counters, every wait
+ *     bounded by the limit of bse_set_wait_limit, BSE_ERR_TIMEOUT if one gives
+ *     up), so it is used only where this handle's kernels run alone: the
+ *     many-site batch keeps the two-pass step.  It takes 2 Nb <= 128,
+ *     N_alpha * n_vec <= 8, a 4^3 or 8^3 k mesh, an even grid and at most 4 k
+ *     points per SM (BSE_ERR_UNSUPPORTED from this call otherwise; calls with
+ *     more vectors fall back to the two-pass step).
+ * In the one-pass kernel the grid->band tiles of a slab are issued, between
+ * band->grid tiles of later slabs, as soon as the slab's k->R / x W / R->k
+ * sums are complete on every CTA; lag (0 = default 2, else 1..3) bounds the
+ * slabs read once but not yet twice to lag + 1 (fewer keep U in L2 between
+ * its two reads, more hide the exchange between CTAs); stages (0 = default
+ * 5, else 2..5): 36 KB pipeline stages of the one-pass kernel; flags (one pass): BSE_SCHED_L2_HINT = TMA cache policies that keep U
+ * in L2 after its first read and drop it after the second.  Results differ from the two-pass step only in the order of
+ * FP32 sums (no split-K partials).  Other precisions: no-op.  Synchronises
+ * the handle's stream. */
+enum { BSE_SCHED_TWO_PASS = 0, BSE_SCHED_TWO_PASS_ROWMAJOR = 1, BSE_SCHED_ONE_PASS = 2 };
+enum { BSE_SCHED_L2_HINT = 1 };
+bse_status bse_set_schedule(bse_handle* h, int schedule, int lag, int stages, int flags);
+/* The handle's schedule (-1 for NULL). */
+int bse_schedule(const bse_handle* h);
 
 /* Failure-detection aid, no counterpart in the paper: every wait of the
  * tensor-core pipeline (a TMA copy landing, an MMA retiring, an accumulator

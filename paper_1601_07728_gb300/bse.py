@@ -26,8 +26,11 @@ EXPORTS = ["bse_setup", "bse_destroy", "bse_dim", "bse_apply_h", "bse_haydock", 
            "bse_gmres", "bse_jacobi_diag", "bse_launch_count", "bse_status_string", "bse_last_error",
            "bse_profile_enable", "bse_profile_read", "bse_kernel_name", "bse_short_range_noalloc",
            "bse_mlp_n_params", "bse_mlp_create", "bse_mlp_destroy", "bse_mlp_params", "bse_mlp_outputs",
-           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0", "bse_set_wait_limit", "bse_rixs", "bse_rixs_emission", "bse_set_slabs", "bse_slabs"]
-KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion"]
+           "bse_mlp_loss_grad", "bse_mlp_adam_step", "bse_mlp_train", "bse_gmres_set_mlp", "bse_haydock_batch", "bse_autotune", "bse_set_tiles", "bse_local_projection", "bse_screening_chi0", "bse_set_wait_limit", "bse_rixs", "bse_rixs_emission", "bse_set_slabs", "bse_slabs",
+           "bse_set_schedule", "bse_schedule"]
+KERNEL_KINDS = ["band_to_grid", "kconv", "grid_to_band", "sr_in", "sr_couple", "prep", "recursion", "one_pass"]
+# schedules of the split-bf16 step (bse_set_schedule)
+SCHEDULES = {"two_pass": 0, "two_pass_rowmajor": 1, "one_pass": 2}
 
 
 class Desc(ctypes.Structure):
@@ -123,6 +126,10 @@ def lib():
     L.bse_set_slabs.restype = ci
     L.bse_slabs.argtypes = [vp]
     L.bse_slabs.restype = ci
+    L.bse_set_schedule.argtypes = [vp, ci, ci, ci, ci]
+    L.bse_set_schedule.restype = ci
+    L.bse_schedule.argtypes = [vp]
+    L.bse_schedule.restype = ci
     L.bse_rixs.argtypes = [vp, vp, vp, vp, ci, vp, cd, ci, ci, ci, ci, vp, vp, vp, vp, vp]
     L.bse_rixs.restype = ci
     L.bse_rixs_emission.argtypes = [vp, ci, ci, cll, vp, ci, vp, vp]
@@ -300,6 +307,18 @@ class System:
     @property
     def slabs(self):
         return int(lib().bse_slabs(self.h))
+
+    def set_schedule(self, schedule, lag=0, stages=0, l2_hint=True):
+        """Schedule of the split-bf16 step: "two_pass", "two_pass_rowmajor" or "one_pass"
+        (one-pass pipeline lag and stages, 0 = defaults; L2 cache policy)."""
+        sc = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+        flags = 1 if l2_hint else 0
+        self._check(lib().bse_set_schedule(self.h, sc, int(lag), int(stages), flags))
+
+    @property
+    def schedule(self):
+        v = int(lib().bse_schedule(self.h))
+        return {b: a for a, b in SCHEDULES.items()}.get(v, v)
 
     def set_wait_limit(self, seconds):
         """Limit of every wait of the tensor-core pipeline (BSE_ERR_TIMEOUT beyond it)."""

@@ -437,7 +437,7 @@ bse_status bse_gmres_set_mlp(bse_handle* h, bse_mlp* m) {
 
 const char* bse_kernel_name(int kind) {
   static const char* names[BSE_K_COUNT] = {"band_to_grid", "kconv", "grid_to_band", "sr_in",
-                                           "sr_couple", "prep", "recursion"};
+                                           "sr_couple", "prep", "recursion", "one_pass"};
   return (kind >= 0 && kind < BSE_K_COUNT) ? names[kind] : "unknown";
 }
 

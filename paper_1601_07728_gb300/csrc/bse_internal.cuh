@@ -98,6 +98,13 @@ struct bse_handle {
   cudaEvent_t ev_side2 = nullptr;
   cudaStream_t cur = nullptr;   // stream the next profiled launch goes to
 
+  // schedule of the split-bf16 step (bse_set_schedule): two passes over U with
+  // the transposed copy, two passes reading U row-major for both, or one pass
+  int sched = 0;
+  int op_lag = 2, op_stages = 5, op_l2hint = 1;
+  int op_max_vec = 0;          // one pass: largest n_vec it takes (0: none)
+  bool concurrent = false;     // kernels of other handles may run beside this one's (many-site graph)
+
   // grow-only device workspace of the Haydock driver (kept between calls)
   void* ws = nullptr;
   size_t ws_cap = 0;
@@ -252,6 +259,9 @@ bse_status bse_kconv_bf16(bse_handle* h, int n_vec);
 bse_status bse_kconv_inplace(bse_handle* h, int n_vec);
 bse_status bse_kconv_split(bse_handle* h, int n_vec, __nv_bfloat16* hi, __nv_bfloat16* lo, int nnmax, int x0, int x1,
                            cudaStream_t st);
+// one-pass step: band->grid, k-transform and grid->band slab by slab in one kernel, then the epilogue
+bse_status bse_tc_apply_onepass(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                                const bse_dotfuse* fuse, bool wait_side);
 // true if the k-transform can run on part of the grid (x-slabs)
 bool bse_kconv_takes_slabs(const bse_handle* h);
 bse_status bse_tc_status(bse_handle* h);   // device error word of the tensor-core pipeline

@@ -2,9 +2,9 @@
 // and the short-range projector terms.
 //
 // Algorithm 1 (Sec. 3.2.1), with the loop over x and alpha turned inside out:
-//   band->grid  phi[k][c][x]  = sum_n  U[k][x][n] psi[c][k][n]   (U = e^{ik.x} u, first line)
-//   k-conv      phi[k][c][x]  <- F_{R->k} W(x,R) F_{k->R} phi     (lines 3-5, k_kconv.cu)
-//   grid->band  out[c][k][n]  = sum_x conj(U[k][x][n]) phi[k][c][x]   (last line)
+//   band->grid  phi[k][c][x]  = sum_n  U[k][x][n] psi[c][k][n]   (U = e^{ik.x} u)
+//   k-conv      phi[k][c][x]  <- F_{R->k} W(x,R) F_{k->R} phi     (k_kconv.cu)
+//   grid->band  out[c][k][n]  = sum_x conj(U[k][x][n]) phi[k][c][x]
 // with c = v*Na + alpha the column index (vector v, core state alpha).  The
 // grid->band kernel also adds E_nk psi - chi psi (Eqs. 3-5) and the short-range
 // projection out (Sec. 3.2.2), so one pass writes H psi.
@@ -366,6 +366,9 @@ bse_status bse_apply_device(bse_handle* h, const double2* psi, double2* hpsi, in
       }
       s = bse_sr_terms(h, psi, n_vec);
       if (s != BSE_OK) return s;
+      // one pass over U (a handle running alone; sizes the one-pass kernel takes)
+      if (h->sched == BSE_SCHED_ONE_PASS && !h->concurrent && n_vec <= h->op_max_vec)
+        return bse_tc_apply_onepass(h, psi, hpsi, n_vec, fuse, h->np > 0);
       if (h->slabs > 1) return bse_tc_apply_slabbed(h, psi, hpsi, n_vec, fuse, h->np > 0);
       s = bse_tc_band_to_grid(h, n_vec);
       if (s != BSE_OK) return s;

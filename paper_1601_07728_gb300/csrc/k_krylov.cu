@@ -1042,7 +1042,10 @@ bse_status bse_haydock_batch_device(bse_handle* const* hs, const double2* const*
       bse_status es = BSE_OK;
       for (int s = 0; s < n_sites && es == BSE_OK; ++s) {
         cudaStreamWaitEvent(hs[s]->stream, ev[n_sites], 0);
+        // sites overlap on the GPU: no kernel whose CTAs wait on one another
+        hs[s]->concurrent = true;
         es = hay_enqueue(hs[s], bs[s], n_vec, n_steps, 0, a_d[s], b_d[s], steps_d[s], frs[s], &status[s], false);
+        hs[s]->concurrent = false;
         cudaEventRecord(ev[s], hs[s]->stream);
         cudaStreamWaitEvent(master, ev[s], 0);
       }

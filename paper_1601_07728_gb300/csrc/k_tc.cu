@@ -2,10 +2,10 @@
 //
 // Both band<->grid contractions are real GEMMs on the re/im-interleaved
 // Bloch functions U~ (U = e^{ik.x} u):
-//   band->grid (first line):  Phi_k[x][j]  = sum_q U~_k[x][q] Bpsi_k[j][q]
+//   band->grid:  Phi_k[x][j]  = sum_q U~_k[x][q] Bpsi_k[j][q]
 //       q = 2n + u (u = re/im part of U), j = 2c + s (s = re/im part of phi_c),
 //       Bpsi holds (psi_r, -psi_i) for s = 0 and (psi_i, psi_r) for s = 1.
-//   grid->band (last line):   D_k[q][j] = sum_x U~_k[x][q] Phi'_k[x][j]
+//   grid->band:  D_k[q][j] = sum_x U~_k[x][q] Phi'_k[x][j]
 //       psi'_{c,n} = (D[2n][2c] + D[2n+1][2c+1]) + i (D[2n][2c+1] - D[2n+1][2c]).
 // Every operand is split v = hi + lo into two bf16 numbers and each product
 // is formed as hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
@@ -18,9 +18,14 @@
 // on timeout the kernel records an error word, drains its own copies and
 // frees its TMEM before returning.
 #include "bse_internal.cuh"
+#include "tc_ptx.cuh"
+#include "k_onepass.cuh"
 
 #include <cuda.h>
 #include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
 
 namespace {
 
@@ -30,119 +35,6 @@ constexpr int TC_THREADS = 192;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
 constexpr int SMEM_BUDGET = 224 * 1024;
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtime() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait (limit_ns of %globaltimer) for the phase of the given parity;
-// false on timeout or abort.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, unsigned long long limit_ns) {
-  if (mbar_try(a, parity)) return true;
-  const unsigned long long t0 = gtime();
-  while (true) {
-    if (mbar_try(a, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtime() - t0 > limit_ns) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
-                                            int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
-          dst),
-      "l"((unsigned long long)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
-                                            int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
-      "[%2];" ::"r"(dst),
-      "l"((unsigned long long)map), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, unsigned long long adesc, unsigned long long bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
-
-// 32 TMEM lanes (this warp's quadrant) x 16 consecutive 32-bit columns
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart (tcgen05 descriptor version 1).
-__device__ __forceinline__ unsigned long long sdesc_sw128(uint32_t saddr) {
-  unsigned long long d = 0;
-  d |= (unsigned long long)((saddr & 0x3FFFFu) >> 4);
-  d |= (unsigned long long)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (unsigned long long)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
-  d |= (unsigned long long)1 << 46;                 // descriptor version
-  d |= (unsigned long long)2 << 61;                 // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor of kind::f16: bf16 A and B (K-major), FP32 D, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
 
 // ---------------------------------------------------------------------------
 // persistent split-bf16 GEMM
@@ -163,6 +55,7 @@ struct TcParams {
   int nk, nx, nb, nc;
   int* err;
   unsigned long long wait_ns;   // limit of each pipeline wait (the drain after an abort keeps WAIT_NS)
+  uint32_t lbo, sbo;   // mode 2: MN-major descriptor offsets of the A operand (bytes)
 };
 
 struct Tile {
@@ -258,6 +151,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tma_load_3d(st + a_bytes, &ma_lo, full(s), kc, tl.mt * TC_M, tl.batch);
           tma_load_3d(st + 2 * a_bytes, &mb_hi, full(s), kc, tl.nt * p.nn, tl.batch);
           tma_load_3d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), kc, tl.nt * p.nn, tl.batch);
+        } else if (p.mode == 2) {
+          // grid->band from the row-major U~ [k][x][q]: rows x = 64 kt .. 64 kt + 63
+          // of q 0..63 and 64..127 of the M tile, an MN-major A operand
+          const int kt = tl.kb0 + kb;
+          const int q0 = tl.mt * TC_M;
+          tma_load_3d(st, &ma_hi, full(s), q0, kt * TC_KB, tl.batch);
+          tma_load_3d(st + a_bytes / 2, &ma_hi, full(s), q0 + TC_KB, kt * TC_KB, tl.batch);
+          tma_load_3d(st + a_bytes, &ma_lo, full(s), q0, kt * TC_KB, tl.batch);
+          tma_load_3d(st + a_bytes + a_bytes / 2, &ma_lo, full(s), q0 + TC_KB, kt * TC_KB, tl.batch);
+          tma_load_4d(st + 2 * a_bytes, &mb_hi, full(s), 0, tl.nt * p.nn, kt, tl.batch);
+          tma_load_4d(st + 2 * a_bytes + b_bytes, &mb_lo, full(s), 0, tl.nt * p.nn, kt, tl.batch);
         } else {
           // K-tiled operands [batch][K/64][rows][64]: one contiguous block per K block
           const int kt = tl.kb0 + kb;
@@ -275,7 +179,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    const uint32_t idesc = idesc_bf16(TC_M, p.nn);
+    const uint32_t idesc = idesc_bf16(TC_M, p.nn) | (p.mode == 2 ? IDESC_A_MN : 0u);
     int it = 0, local = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++local) {
@@ -300,8 +204,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t st = sbase + (uint32_t)s * stage_bytes;
 #pragma unroll
         for (int ks = 0; ks < TC_KB / 16; ++ks) {
-          const unsigned long long a_hi = sdesc_sw128(st + ks * 32);
-          const unsigned long long a_lo = sdesc_sw128(st + a_bytes + ks * 32);
+          // K-major A: 16 K elements = 32 bytes along the row; MN-major A (mode 2):
+          // 16 rows of K = 2048 bytes
+          const unsigned long long a_hi =
+              p.mode == 2 ? sdesc_mn_sw128(st + ks * 2048, p.lbo, p.sbo) : sdesc_sw128(st + ks * 32);
+          const unsigned long long a_lo = p.mode == 2 ? sdesc_mn_sw128(st + a_bytes + ks * 2048, p.lbo, p.sbo)
+                                                      : sdesc_sw128(st + a_bytes + ks * 32);
           const unsigned long long b_hi = sdesc_sw128(st + 2 * a_bytes + ks * 32);
           const unsigned long long b_lo = sdesc_sw128(st + 2 * a_bytes + b_bytes + ks * 32);
           mma_bf16(d, a_hi, b_hi, idesc, (kb | ks) != 0);
@@ -334,7 +242,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       Tile tl = decode(p, t);
       const int acc = local & 1;
       const uint32_t aph = (uint32_t)(local >> 1) & 1u;
-      if (!mbar_wait(tfull(acc), aph, abort_flag, p.wait_ns)) {
+      // the lanes agree on the outcome before the warp-wide tensor-memory load
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull(acc), aph, abort_flag, p.wait_ns))) {
         if (lane == 0) {
           atomicExch(p.err, 1);
           *abort_flag = 1;
@@ -903,10 +812,20 @@ struct TcState {
   int stages = 0;       // pipeline stages (0: chosen by rule per tile width)
   int part_cap = 0;     // split-K factor the partial buffer is sized for
   int* err = nullptr;   // device error word
-  CUtensorMap a2_hi, a2_lo, a6_hi, a6_lo;
+  unsigned* sync = nullptr;   // one-pass step: per-slab counters, abort and done words
+  uint32_t lbo = 8192, sbo = 1024;   // MN-major descriptors: q blocks 8 KB apart, 8-row groups 1 KB apart
+  // a2: U~ row-major, box 64 x 128 rows (band->grid A); a2m: the same array,
+  // box 64 x 64 rows (grid->band A read MN-major); a6: the K-tiled transposed copy
+  CUtensorMap a2_hi, a2_lo, a2m_hi, a2m_lo, a6_hi, a6_lo;
 };
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// error word (offset 0) and, from offset 256, the one-pass step's counters
+size_t tc_word_bytes(const bse_handle* h) {
+  const size_t nslab = (size_t)(h->nx + TC_M - 1) / TC_M;
+  return 256 + ((2 * nslab + 3) * sizeof(unsigned) + 255) / 256 * 256;
+}
 
 // MMA N of one tile for `rows` B rows (two per complex column): one tile up
 // to 256 rows (the tcgen05 maximum, two accumulators filling TMEM's 512
@@ -940,6 +859,8 @@ bse_status launch_gemm(bse_handle* h, TcState* ts, int mode, const CUtensorMap& 
   p.tmem_cols = cols;
   p.err = ts->err;
   p.wait_ns = h->tc_wait_ns;
+  p.lbo = ts->lbo;
+  p.sbo = ts->sbo;
   const size_t smem = 1024 + (size_t)p.stages * (2 * TC_M * 128 + 2 * p.nn * 128) + 256;
   cudaFuncSetAttribute(tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = p.ntiles < ts->sms ? p.ntiles : ts->sms;
@@ -978,16 +899,19 @@ bse_status bse_tc_prepare(bse_handle* h) {
     if (s == BSE_OK)
       s = bse_handle_malloc(h, (void**)&h->part,
                             (size_t)ts->smax * h->nk * h->nb * h->na * h->max_vec * sizeof(float2), "split-K partials");
-    if (s == BSE_OK) s = bse_handle_malloc(h, (void**)&h->tmap, 256, "tensor-core error word");
+    if (s == BSE_OK) s = bse_handle_malloc(h, (void**)&h->tmap, tc_word_bytes(h), "tensor-core error and sync words");
     if (s != BSE_OK) return s;
   }
   ts->err = (int*)h->tmap;
-  cudaMemsetAsync(ts->err, 0, 256, h->stream);
+  ts->sync = (unsigned*)((char*)h->tmap + 256);
+  cudaMemsetAsync(h->tmap, 0, tc_word_bytes(h), h->stream);
   cudaMemsetAsync(h->bphi, 0, 2 * nbf * sizeof(__nv_bfloat16), h->stream);
   cudaMemsetAsync(h->bpsi, 0, 2 * nbp * sizeof(__nv_bfloat16), h->stream);
   const int kp = ts->kp;
   bool ok = make_map(&ts->a2_hi, h->u_hi, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
             make_map(&ts->a2_lo, h->u_lo, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_M) &&
+            make_map(&ts->a2m_hi, h->u_hi, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_KB) &&
+            make_map(&ts->a2m_lo, h->u_lo, kp, h->nx, h->nk, kp, (uint64_t)h->nx * kp, TC_KB) &&
             make_map_tiled(&ts->a6_hi, h->ut_hi, 2 * h->nb, 2 * h->nb, x64, h->nk, TC_M) &&
             make_map_tiled(&ts->a6_lo, h->ut_lo, 2 * h->nb, 2 * h->nb, x64, h->nk, TC_M);
   if (!ok) return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
@@ -1067,7 +991,7 @@ bse_status g2b_range(bse_handle* h, int n_vec, int kb_b, int kb_e, int split_bas
       !make_map_tiled(&b_lo, h->bphi + nbf, rows, ts->nnmax, x64, h->nk, nn))
     return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
   TcParams p{};
-  p.mode = 1;
+  p.mode = h->sched == BSE_SCHED_TWO_PASS_ROWMAJOR ? 2 : 1;
   p.mtiles = (2 * h->nb + TC_M - 1) / TC_M;
   p.kb_base = kb_b;
   p.kb_total = kb_e - kb_b;
@@ -1085,6 +1009,7 @@ bse_status g2b_range(bse_handle* h, int n_vec, int kb_b, int kb_e, int split_bas
   p.nb = h->nb;
   p.nc = nc;
   *nsplit_out = p.nsplit;
+  if (p.mode == 2) return launch_gemm(h, ts, 2, ts->a2m_hi, ts->a2m_lo, b_hi, b_lo, p, BSE_K_GRID_TO_BAND, st);
   return launch_gemm(h, ts, 1, ts->a6_hi, ts->a6_lo, b_hi, b_lo, p, BSE_K_GRID_TO_BAND, st);
 }
 
@@ -1150,6 +1075,100 @@ bse_status bse_tc_grid_to_band(bse_handle* h, const double2* psi, double2* hpsi,
   if (s != BSE_OK) return s;
   return g2b_epilogue(h, psi, hpsi, n_vec, fuse, wait_side, ns);
 }
+
+// One-pass step (k_onepass.cu) for one pass over n_vec vectors: band->grid,
+// k-transform and grid->band slab by slab in one persistent kernel, then the
+// grid->band epilogue on its single partial-sum slot.
+bse_status bse_tc_apply_onepass(bse_handle* h, const double2* psi, double2* hpsi, int n_vec,
+                                const bse_dotfuse* fuse, bool wait_side) {
+  TcState* ts = (TcState*)h->tmap_host;
+  const int rows = 16;
+  const size_t nbp = (size_t)h->nk * ts->nnmax * ts->kp;
+  const uint64_t x64 = (uint64_t)(h->nx + TC_KB - 1) / TC_KB;
+  const size_t nbf = (size_t)h->nk * x64 * ts->nnmax * TC_KB;
+  CUtensorMap maps[8];
+  maps[0] = ts->a2_hi;
+  maps[1] = ts->a2_lo;
+  maps[2] = ts->a2m_hi;
+  maps[3] = ts->a2m_lo;
+  if (!make_map(&maps[4], h->bpsi, ts->kp, rows, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, rows) ||
+      !make_map(&maps[5], h->bpsi + nbp, ts->kp, rows, h->nk, ts->kp, (uint64_t)ts->nnmax * ts->kp, rows) ||
+      !make_map_tiled(&maps[6], h->bphi, rows, ts->nnmax, x64, h->nk, rows) ||
+      !make_map_tiled(&maps[7], h->bphi + nbf, rows, ts->nnmax, x64, h->nk, rows))
+    return bse_fail(h, BSE_ERR_CUDA, "tensor map encoding failed");
+  OnePassParams p{};
+  p.nk = h->nk;
+  p.nx = h->nx;
+  p.nb = h->nb;
+  p.nc = n_vec * h->na;
+  p.nslab = (h->nx + TC_M - 1) / TC_M;
+  p.kb_b2g = (ts->kp + TC_KB - 1) / TC_KB;
+  p.lag = h->op_lag;
+  p.stages = h->op_stages;
+  p.tmem_cols = 128;
+  p.nnmax = ts->nnmax;
+  p.lbo = (int)ts->lbo;
+  p.sbo = (int)ts->sbo;
+  p.l2hint = h->op_l2hint;
+  p.phi = (float2*)h->phi;
+  p.part = (float2*)h->part;
+  p.bphi_hi = h->bphi;
+  p.bphi_lo = h->bphi + nbf;
+  p.w = (const float*)h->w;
+  p.sync = ts->sync;
+  p.err = ts->err;
+  p.wait_ns = h->tc_wait_ns;
+  // as few k per CTA as the SMs allow, the same number on every CTA (the slab
+  // counters pace every CTA to the busiest); SMs left over run the
+  // short-range kernels of the side stream
+  const int kpc = (h->nk + ts->sms - 1) / ts->sms;
+  const int grid = (h->nk + kpc - 1) / kpc;
+  cudaError_t e = cudaSuccess;
+  BSE_PROF(h, BSE_K_ONE_PASS, e = bse_onepass_launch(h->nk3[0], grid, maps, p, h->stream));
+  if (e != cudaSuccess) return bse_cuda_check(h, e, "one-pass launch");
+  return g2b_epilogue(h, psi, hpsi, n_vec, fuse, wait_side, 1);
+}
+
+namespace {
+// largest n_vec the one-pass step takes on this handle (0: none)
+int onepass_max_vec(const bse_handle* h, int stages) {
+  const TcState* ts = (const TcState*)h->tmap_host;
+  if (!ts || h->prec != BSE_PREC_SPLIT_BF16 || h->na > 8) return 0;
+  if (2 * h->nb > TC_M || ts->kp > 2 * TC_KB || !bse_kconv_takes_slabs(h)) return 0;
+  const int grid = std::min(ts->sms, h->nk);
+  if (grid < 1 || (h->nk + grid - 1) / grid > OP_MAX_KPC) return 0;
+  if (bse_onepass_smem(h->nk3[0], stages) > 227 * 1024) return 0;
+  if (bse_onepass_max_blocks_per_sm(h->nk3[0], stages) < 1) return 0;
+  return std::min(8 / h->na, h->max_vec);
+}
+}  // namespace
+
+// Schedule of the split-bf16 step (see bse_set_schedule in bse.h).
+extern "C" bse_status bse_set_schedule(bse_handle* h, int schedule, int lag, int stages, int flags) {
+  if (!h) return BSE_ERR_INVALID_ARG;
+  if (schedule < BSE_SCHED_TWO_PASS || schedule > BSE_SCHED_ONE_PASS || lag < 0 || lag > 3 || stages < 0 ||
+      stages == 1 || stages > 5 || flags < 0 || flags > 1)
+    return bse_fail(h, BSE_ERR_INVALID_ARG,
+                    "set_schedule: need schedule 0..2, lag 0..3, stages 0 or 2..5, flags 0 or 1");
+  if (h->prec != BSE_PREC_SPLIT_BF16 || !h->tmap_host) return BSE_OK;
+  if (lag == 0) lag = 2;
+  if (stages == 0) stages = 5;
+  if (schedule == BSE_SCHED_ONE_PASS && onepass_max_vec(h, stages) < 1)
+    return bse_fail(h, BSE_ERR_UNSUPPORTED,
+                    "set_schedule: the one-pass step needs 2 Nb <= 128, N_alpha <= 8, a 4^3 or 8^3 k mesh, an "
+                    "even grid and at most 4 k points per SM");
+  const bse_status ss = bse_cuda_check(h, cudaStreamSynchronize(h->stream), "set_schedule sync");
+  if (ss != BSE_OK) return ss;
+  h->sched = schedule;
+  h->op_lag = lag;
+  h->op_stages = stages;
+  h->op_l2hint = flags & BSE_SCHED_L2_HINT ? 1 : 0;
+  h->op_max_vec = schedule == BSE_SCHED_ONE_PASS ? onepass_max_vec(h, stages) : 0;
+  bse_drop_graph(h);
+  return BSE_OK;
+}
+
+extern "C" int bse_schedule(const bse_handle* h) { return h ? h->sched : -1; }
 
 // The step in x-slabs: band->grid of every slab on the handle's stream, and
 // for each slab, once its band->grid is done, the k-transform and grid->band

@@ -59,6 +59,9 @@ def test_null_handle_calls(L):
     assert L.bse_autotune(None, 1, 1, None, None) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_set_tiles(None, 2, 4) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_set_wait_limit(None, 1.0) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_set_schedule(None, 2, 0, 0, 1) == bse.BSE_ERR_INVALID_ARG
+    assert L.bse_schedule(None) == -1
+    assert L.bse_kernel_name(7) == b"one_pass"
     assert L.bse_haydock(None, None, 1, 1, 0, None, None, None) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_gmres(None, None, None, 1, 1e-6, 30, 100, 0, None, None, None) == bse.BSE_ERR_INVALID_ARG
     assert L.bse_mlp_train(None, None, 1, None, 1, 1, 1, 1e-3, 0, 10, None, None) == bse.BSE_ERR_INVALID_ARG
