@@ -79,6 +79,8 @@ def parse():
                    help="timed Haydock steps on the 48^3-grid supercell workload (0 = skip)")
     p.add_argument("--no-one-pass", action="store_true",
                    help="skip the leg that times the one-pass schedule (bse_set_schedule one_pass)")
+    p.add_argument("--one-pass-lag", type=int, default=2,
+                   help="one-pass schedule: slabs read once but not yet twice, beyond the current one")
     p.add_argument("--sites", type=int, default=8,
                    help="sites of the many-site workload run in one batched launch of 200 steps (0 = skip)")
     return p.parse_args()
@@ -497,7 +499,7 @@ def main():
     if not args.no_one_pass and args.precision == "split_bf16":
         sys1 = bse.System(s, precision=args.precision, max_vec=1, stream=stream.cuda_stream)
         try:
-            sys1.set_schedule("one_pass")
+            sys1.set_schedule("one_pass", lag=args.one_pass_lag)
         except bse.BSEError as ex:
             onep = {"unavailable": str(ex)}
         else:
@@ -515,7 +517,7 @@ def main():
             k_ms = t1 / max(n1, 1)
             pk, _ = peaks()
             onep = {"matvecs_per_s": job_rate(done1, ms1 / 1e3, world), "ms_per_step": ms1 / K, "steps": K,
-                    "lag": 2, "stages": 5, "kernel_ms": k_ms, "kernel_launches": n1,
+                    "lag": args.one_pass_lag, "stages": 5, "kernel_ms": k_ms, "kernel_launches": n1,
                     "alg_bytes_per_launch": alg1, "achieved_gbs": alg1 / (k_ms / 1e3) / 1e9,
                     "frac_of_hbm_peak": alg1 / (k_ms / 1e3) / 1e9 / pk,
                     "two_read_bytes_frac": (alg1 + u1) / (k_ms / 1e3) / 1e9 / pk,

@@ -425,8 +425,8 @@ int bse_slabs(const bse_handle* h);
  *     bounded by the limit of bse_set_wait_limit, BSE_ERR_TIMEOUT if one gives
  *     up), so it is used only where this handle's kernels run alone: the
  *     many-site batch keeps the two-pass step.  It takes 2 Nb <= 128,
- *     N_alpha * n_vec <= 8, a 4^3 or 8^3 k mesh, an even grid and at most 4 k
- *     points per SM (BSE_ERR_UNSUPPORTED from this call otherwise; calls with
+ *     N_alpha * n_vec <= 8, a 4^3 or 8^3 k mesh, a grid of a multiple of 8
+ *     points and at most 4 k points per SM (BSE_ERR_UNSUPPORTED from this call otherwise; calls with
  *     more vectors fall back to the two-pass step).
  * In the one-pass kernel the grid->band tiles of a slab are issued, between
  * band->grid tiles of later slabs, as soon as the slab's k->R / x W / R->k

@@ -59,6 +59,11 @@ constexpr unsigned long long DRAIN_NS = 2000000000ull;
 // band->grid tile (hands the accumulator to the epilogue)
 constexpr int REC_B2G = 1, REC_G2B = 2, REC_FIRST = 4, REC_LAST = 8;
 
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
+  const __nv_bfloat162 v = __halves2bfloat162(lo_half, hi_half);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 // grid-wide abort word and error word after a failed wait
 __device__ __forceinline__ void op_raise(const OnePassParams& p, volatile int* labort) {
   atomicExch(p.err, 1);
@@ -115,45 +120,58 @@ __device__ __forceinline__ int slab_units(const OnePassParams& p, int s) {
   return ((slab_points(p, s) + KC_XW - 1) / KC_XW) * p.nc;
 }
 
-// One k-transform unit: column c, grid points xbase .. xbase + 7, every k.
-// Thread tid = (pencil group g, x pair xp) owns one pencil per pass; the
-// 5-pass pencil scheme of kconv_cubic2 (first forward pass fused into the
-// load, W between the forward and inverse transforms along axis 0, last
-// inverse pass fused into the bf16 hi/lo store of the grid->band operand).
+// One k-transform unit: column c, the 8 grid points of block xb (xb*8 ..
+// xb*8 + 7), every k.  Its band->grid results are contiguous (unit-major
+// Phi, written so by the epilogue) and arrive in the shared tile by one bulk
+// copy; thread tid = (pencil group g, x pair xp) then owns one pencil per
+// pass: forward along axes 2, 1, 0, W(x, R)/Nk, inverse along axes 0, 1, 2.
+// The four threads of a pencil group hold the 8 grid points of a row of the
+// K-tiled grid->band operand between them; a 4 x 4 lane transpose gives each
+// of them 16 contiguous bytes (8 points of one bf16 plane of re or im) per k.
 template <int N>
-__device__ __forceinline__ void kc_unit(const OnePassParams& p, float4* S, int c, int xbase, int tid) {
+__device__ __forceinline__ bool kc_unit(const OnePassParams& p, float4* S, uint32_t kc_bar, uint32_t phase, int c,
+                                        int xb, int tid, volatile int* labort, volatile int* kc_fail) {
   constexpr int NK = N * N * N, NP = N * N;
   constexpr int XP = KC_XW / 2;
   constexpr int NG = KC_THREADS / XP;
-  static_assert(NP <= NG, "one pencil per thread and pass");
+  static_assert(NP <= NG && XP == 4, "one pencil per thread and pass; four x pairs per unit");
   const int xp = tid & (XP - 1), g = tid / XP;
+  const int xbase = xb * KC_XW;
   const int x = xbase + 2 * xp;
-  const bool xin = x < p.nx;   // the grid size is even, so x + 1 < nx too
   const bool act = g < NP;
-  const size_t colstride = (size_t)p.nc * p.nx;
-  const float2* base = p.phi + (size_t)c * p.nx + x;
-  float2 tw[N];   // the radix-2/4/8 butterflies take no twiddle table
-#pragma unroll
-  for (int j = 0; j < N; ++j) tw[j] = make_float2(0.f, 0.f);
-  // W(x, R)/Nk of pass C, loaded with pass A's data so both latencies overlap
+  // W(x, R)/Nk of pass C, loaded while the tile arrives
   float2 wr[N];
   {
     const float inv = 1.f / (float)NK;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      wr[j] = act && xin ? __ldg(reinterpret_cast<const float2*>(p.w + (size_t)(j * NP + g) * p.nx + x))
-                         : make_float2(0.f, 0.f);
+      wr[j] = act ? __ldg(reinterpret_cast<const float2*>(p.w + (size_t)(j * NP + g) * p.nx + x))
+                  : make_float2(0.f, 0.f);
       wr[j].x *= inv;
       wr[j].y *= inv;
     }
   }
-  // pass A: load (L2: written by other CTAs during this launch) + forward along axis 2
+  if (tid == 0) {
+    // Phi of the unit, [k][8 points], written by other CTAs (made visible by
+    // the acquire of the band->grid counter): read through the async proxy
+    fence_proxy_async_global();
+    mbar_expect_tx(kc_bar, NK * KC_XW * 8);
+    bulk_load(smem_u32(S), p.phi + ((size_t)xb * p.nc + c) * NK * KC_XW, NK * KC_XW * 8, kc_bar);
+  }
+  // every thread of the unit takes the same branch: a failed wait is agreed on
+  // through shared memory (set once, never cleared: the role then ends)
+  if (!op_mbar_wait(p, kc_bar, phase, labort)) *kc_fail = 1;
+  named_bar_sync(1, KC_THREADS);
+  if (*kc_fail) return false;
+  float2 tw[N];   // the radix-2/4/8 butterflies take no twiddle table
+#pragma unroll
+  for (int j = 0; j < N; ++j) tw[j] = make_float2(0.f, 0.f);
+  // pass A: forward along axis 2 (k = g N + j)
   if (act) {
     float2 va[N], vb[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (xin) q = __ldcg(reinterpret_cast<const float4*>(base + (size_t)(g * N + j) * colstride));
+      const float4 q = S[(g * N + j) * XP + xp];
       va[j] = make_float2(q.x, q.y);
       vb[j] = make_float2(q.z, q.w);
     }
@@ -219,8 +237,8 @@ __device__ __forceinline__ void kc_unit(const OnePassParams& p, float4* S, int c
     for (int j = 0; j < N; ++j) S[(kb + j * N) * XP + xp] = make_float4(va[j].x, va[j].y, vb[j].x, vb[j].y);
   }
   named_bar_sync(1, KC_THREADS);
-  // pass E: inverse along axis 2 + bf16 hi/lo store, K-tiled planes
-  // [k][x/64][row][64] with rows 2c (re) and 2c + 1 (im)
+  // pass E: inverse along axis 2, bf16 hi/lo split, and the store to the
+  // K-tiled planes [k][x/64][row][64] (rows 2c = re, 2c + 1 = im)
   if (act) {
     float2 va[N], vb[N];
 #pragma unroll
@@ -231,24 +249,43 @@ __device__ __forceinline__ void kc_unit(const OnePassParams& p, float4* S, int c
     }
     dftN<float, N, -1>(va, tw);
     dftN<float, N, -1>(vb, tw);
-    if (xin) {
-      const size_t x64 = (size_t)((p.nx + 63) >> 6);
+    const size_t x64 = (size_t)((p.nx + 63) >> 6);
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
+    for (int j = 0; j < N; ++j) {
+      // this thread's two points as bf16 pairs: kind 0 = re hi, 1 = re lo, 2 = im hi, 3 = im lo
+      __nv_bfloat16 h0, l0, h1, l1, h2, l2, h3, l3;
+      split_bf(va[j].x, h0, l0);
+      split_bf(vb[j].x, h1, l1);
+      split_bf(va[j].y, h2, l2);
+      split_bf(vb[j].y, h3, l3);
+      uint32_t w[4];
+      w[0] = bf2_bits(h0, h1);
+      w[1] = bf2_bits(l0, l1);
+      w[2] = bf2_bits(h2, h3);
+      w[3] = bf2_bits(l2, l3);
+      // lane xp keeps kind xp of all four x pairs: out[m] = kind xp of x pair m
+      uint32_t out[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int send = (xp + r) & 3, from = (xp - r) & 3;
+        const uint32_t v = send == 0 ? w[0] : send == 1 ? w[1] : send == 2 ? w[2] : w[3];
+        // whole warps are active here (pencil groups fill warps), each lane
+        // reading from its own group of four
+        const uint32_t got = __shfl_sync(0xffffffffu, v, (threadIdx.x & 28) | from);
+        out[0] = from == 0 ? got : out[0];
+        out[1] = from == 1 ? got : out[1];
+        out[2] = from == 2 ? got : out[2];
+        out[3] = from == 3 ? got : out[3];
+      }
+      if (xbase < p.nx) {
         const int k = g * N + j;
-        const size_t o = (((size_t)k * x64 + (x >> 6)) * p.nnmax + 2 * c) * 64 + (x & 63);
-        __nv_bfloat16 h0, l0, h1, l1, h2, l2, h3, l3;
-        split_bf(va[j].x, h0, l0);
-        split_bf(vb[j].x, h1, l1);
-        split_bf(va[j].y, h2, l2);
-        split_bf(vb[j].y, h3, l3);
-        *reinterpret_cast<__nv_bfloat162*>(p.bphi_hi + o) = __halves2bfloat162(h0, h1);
-        *reinterpret_cast<__nv_bfloat162*>(p.bphi_lo + o) = __halves2bfloat162(l0, l1);
-        *reinterpret_cast<__nv_bfloat162*>(p.bphi_hi + o + 64) = __halves2bfloat162(h2, h3);
-        *reinterpret_cast<__nv_bfloat162*>(p.bphi_lo + o + 64) = __halves2bfloat162(l2, l3);
+        const size_t o = (((size_t)k * x64 + (xbase >> 6)) * p.nnmax + 2 * c + (xp >> 1)) * 64 + (xbase & 63);
+        __nv_bfloat16* dst = (xp & 1) ? p.bphi_lo : p.bphi_hi;
+        *reinterpret_cast<uint4*>(dst + o) = make_uint4(out[0], out[1], out[2], out[3]);
       }
     }
   }
+  return true;
 }
 
 template <int N>
@@ -263,8 +300,8 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
   const int S = p.stages;
   float4* kc_tile = (float4*)(sm + (size_t)S * STAGE_BYTES);
   unsigned long long* bars = (unsigned long long*)(sm + (size_t)S * STAGE_BYTES + (size_t)N * N * N * KC_XW * 8);
-  // bars: full[S], empty[S], tfull[2], tempty[2], gfin
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 5);
+  // bars: full[S], empty[S], tfull[2], tempty[2], gfin, kc (k-transform tile copy)
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 6);
   volatile int* labort = (volatile int*)(tmem_slot + 1);
   int* consumed = (int*)(tmem_slot + 2);
   int* issued = (int*)(tmem_slot + 3);
@@ -272,12 +309,14 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
   // slabs whose k-transform is complete on every CTA (set by the poller warp)
   int* kc_ready = (int*)(tmem_slot + 4 + OP_MAX_STAGES);
   const uint32_t kc_ready_a = smem_u32(kc_ready);
+  volatile int* kc_fail = (volatile int*)(kc_ready + 1);   // a k-transform tile copy gave up
   const uint32_t sbase = smem_u32(sm);
   auto full = [&](int s) { return smem_u32(&bars[s]); };
   auto empty = [&](int s) { return smem_u32(&bars[S + s]); };
   auto tfull = [&](int a) { return smem_u32(&bars[2 * S + a]); };
   auto tempty = [&](int a) { return smem_u32(&bars[2 * S + 2 + a]); };
   const uint32_t gfin = smem_u32(&bars[2 * S + 4]);
+  const uint32_t kc_bar = smem_u32(&bars[2 * S + 5]);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
   unsigned* b2g_cnt = p.sync;              // [nslab]
@@ -298,10 +337,12 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
       mbar_init(tempty(a), 4);
     }
     mbar_init(gfin, 1);
+    mbar_init(kc_bar, 1);
     *labort = 0;
     *consumed = 0;
     *issued = 0;
     *kc_ready = 0;
+    *kc_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -534,9 +575,11 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * OP_NN), v);
         const int x = t * OP_M + row_in_tile;
         if (x < p.nx) {
+          // unit-major Phi [x/8][c][k][x%8]: a k-transform unit's input is contiguous
 #pragma unroll
           for (int c = 0; c < 8; ++c)
-            if (c < p.nc) p.phi[((size_t)myk[i] * p.nc + c) * p.nx + x] = make_float2(v[2 * c], v[2 * c + 1]);
+            if (c < p.nc)
+              p.phi[(((size_t)(x >> 3) * p.nc + c) * p.nk + myk[i]) * KC_XW + (x & 7)] = make_float2(v[2 * c], v[2 * c + 1]);
         }
         tc_fence_before();
         __syncwarp();
@@ -585,6 +628,7 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
     // ---------------- k-transform units ----------------
     const int tid = threadIdx.x - 192;
     __shared__ int kc_go;
+    unsigned kc_phase = 0;   // completed copies into the k-transform tile
     const int nu_full = (OP_M / KC_XW) * p.nc;
     for (int s = 0; s < p.nslab; ++s) {
       const int nu = slab_units(p, s);
@@ -597,8 +641,11 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
         if (tid == 0) op_raise(p, labort);
         break;
       }
-      for (int u = first; u < nu; u += G) {
-        kc_unit<N>(p, kc_tile, u % p.nc, s * OP_M + (u / p.nc) * KC_XW, tid);
+      bool unit_ok = true;
+      for (int u = first; u < nu && unit_ok; u += G, ++kc_phase) {
+        unit_ok = kc_unit<N>(p, kc_tile, kc_bar, kc_phase & 1u, u % p.nc, s * (OP_M / KC_XW) + u / p.nc, tid, labort,
+                             kc_fail);
+        if (!unit_ok) break;
         // the unit's Phi' stores precede the barrier; one fence by the thread
         // that publishes the unit
         named_bar_sync(1, KC_THREADS);
@@ -606,6 +653,10 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
           __threadfence();
           atomicAdd(kc_cnt + s, 1u);
         }
+      }
+      if (!unit_ok) {
+        if (tid == 0) op_raise(p, labort);
+        break;
       }
     }
   }

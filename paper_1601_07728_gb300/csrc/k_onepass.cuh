@@ -19,7 +19,7 @@ struct OnePassParams {
   int nnmax;                   // row stride of the grid->band operand planes
   int lbo, sbo;                // MN-major descriptor offsets of the grid->band A operand (bytes)
   int l2hint;                  // keep U~ in L2 between its two reads (TMA cache policies)
-  float2* phi;                 // [nk][nc][nx] band->grid result (FP32)
+  float2* phi;                 // band->grid result (FP32), unit-major [nx/8][nc][nk][8]
   float2* part;                // [nk][nc][nb] grid->band result
   __nv_bfloat16* bphi_hi;      // grid->band operand planes [nk][ceil(nx/64)][nnmax][64]
   __nv_bfloat16* bphi_lo;

@@ -1134,7 +1134,7 @@ namespace {
 int onepass_max_vec(const bse_handle* h, int stages) {
   const TcState* ts = (const TcState*)h->tmap_host;
   if (!ts || h->prec != BSE_PREC_SPLIT_BF16 || h->na > 8) return 0;
-  if (2 * h->nb > TC_M || ts->kp > 2 * TC_KB || !bse_kconv_takes_slabs(h)) return 0;
+  if (2 * h->nb > TC_M || ts->kp > 2 * TC_KB || h->nx % 8 != 0 || !bse_kconv_takes_slabs(h)) return 0;
   const int grid = std::min(ts->sms, h->nk);
   if (grid < 1 || (h->nk + grid - 1) / grid > OP_MAX_KPC) return 0;
   if (bse_onepass_smem(h->nk3[0], stages) > 227 * 1024) return 0;
@@ -1155,8 +1155,8 @@ extern "C" bse_status bse_set_schedule(bse_handle* h, int schedule, int lag, int
   if (stages == 0) stages = 5;
   if (schedule == BSE_SCHED_ONE_PASS && onepass_max_vec(h, stages) < 1)
     return bse_fail(h, BSE_ERR_UNSUPPORTED,
-                    "set_schedule: the one-pass step needs 2 Nb <= 128, N_alpha <= 8, a 4^3 or 8^3 k mesh, an "
-                    "even grid and at most 4 k points per SM");
+                    "set_schedule: the one-pass step needs 2 Nb <= 128, N_alpha <= 8, a 4^3 or 8^3 k mesh, a "
+                    "grid of a multiple of 8 points and at most 4 k points per SM");
   const bse_status ss = bse_cuda_check(h, cudaStreamSynchronize(h->stream), "set_schedule sync");
   if (ss != BSE_OK) return ss;
   h->sched = schedule;

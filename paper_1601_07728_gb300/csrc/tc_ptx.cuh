@@ -140,6 +140,13 @@ __device__ __forceinline__ unsigned long long sdesc_mn_sw128(uint32_t saddr, uin
 // kind::f16 instruction-descriptor bit: A operand MN-major (transposed)
 constexpr uint32_t IDESC_A_MN = 1u << 15;
 
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"((unsigned long long)src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
 // TMA load with an L2 cache policy (createpolicy) attached
 __device__ __forceinline__ void tma_load_3d_hint(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
                                                  int c2, unsigned long long policy) {

@@ -157,9 +157,11 @@ def test_schedule_arguments_checked():
             sysg.set_schedule(**kw)
         assert e.value.status == bse.BSE_ERR_INVALID_ARG
     sysg.close()
-    # 2 Nb > 128 and a 2x3x2 mesh: the one-pass kernel does not take them
+    # 2 Nb > 128, a 2x3x2 mesh, a grid of 180 points (not whole 8-point
+    # k-transform units): the one-pass kernel does not take them
     for kw in (dict(seed=6, n_alpha=1, nk=(4, 4, 4), n_bands=80, nx=(6, 6, 4), n_proj=0),
-               dict(seed=7, n_alpha=2, nk=(2, 3, 2), n_bands=8, nx=(4, 4, 4), n_proj=1)):
+               dict(seed=7, n_alpha=2, nk=(2, 3, 2), n_bands=8, nx=(4, 4, 4), n_proj=1),
+               dict(seed=9, n_alpha=1, nk=(4, 4, 4), n_bands=8, nx=(6, 6, 5), n_proj=0)):
         g = bse.System(S.tiny_system(**kw), precision="split_bf16")
         with pytest.raises(bse.BSEError) as e:
             g.set_schedule("one_pass")
