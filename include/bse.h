@@ -424,7 +424,10 @@ int bse_slabs(const bse_handle* h);
  *     per H psi.  Its CTAs wait on one another (per-slab counters, every wait
  *     bounded by the limit of bse_set_wait_limit, BSE_ERR_TIMEOUT if one gives
  *     up), so it is used only where this handle's kernels run alone: the
- *     many-site batch keeps the two-pass step.  It takes 2 Nb <= 128,
+ *     many-site batch keeps the two-pass step; one-pass steps of two handles
+ *     must not run at the same time on different streams (each would hold
+ *     SMs the other's CTAs wait for, until both give up with
+ *     BSE_ERR_TIMEOUT).  It takes 2 Nb <= 128,
  *     N_alpha * n_vec <= 8, a 4^3 or 8^3 k mesh, a grid of a multiple of 8
  *     points and at most 4 k points per SM (BSE_ERR_UNSUPPORTED from this call otherwise; calls with
  *     more vectors fall back to the two-pass step).
