@@ -130,7 +130,8 @@ __device__ __forceinline__ int slab_units(const OnePassParams& p, int s) {
 // of them 16 contiguous bytes (8 points of one bf16 plane of re or im) per k.
 template <int N>
 __device__ __forceinline__ bool kc_unit(const OnePassParams& p, float4* S, uint32_t kc_bar, uint32_t phase, int c,
-                                        int xb, int tid, volatile int* labort, volatile int* kc_fail) {
+                                        int xb, int tid, volatile int* labort, volatile int* kc_fail,
+                                        volatile int* kc_copies) {
   constexpr int NK = N * N * N, NP = N * N;
   constexpr int XP = KC_XW / 2;
   constexpr int NG = KC_THREADS / XP;
@@ -155,6 +156,7 @@ __device__ __forceinline__ bool kc_unit(const OnePassParams& p, float4* S, uint3
     // Phi of the unit, [k][8 points], written by other CTAs (made visible by
     // the acquire of the band->grid counter): read through the async proxy
     fence_proxy_async_global();
+    kc_copies[0] += 1;   // issued (the abort drain waits for copies not seen to land)
     mbar_expect_tx(kc_bar, NK * KC_XW * 8);
     bulk_load(smem_u32(S), p.phi + ((size_t)xb * p.nc + c) * NK * KC_XW, NK * KC_XW * 8, kc_bar);
   }
@@ -163,6 +165,7 @@ __device__ __forceinline__ bool kc_unit(const OnePassParams& p, float4* S, uint3
   if (!op_mbar_wait(p, kc_bar, phase, labort)) *kc_fail = 1;
   named_bar_sync(1, KC_THREADS);
   if (*kc_fail) return false;
+  if (tid == 0) kc_copies[1] = kc_copies[0];   // landed
   float2 tw[N];   // the radix-2/4/8 butterflies take no twiddle table
 #pragma unroll
   for (int j = 0; j < N; ++j) tw[j] = make_float2(0.f, 0.f);
@@ -310,6 +313,7 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
   int* kc_ready = (int*)(tmem_slot + 4 + OP_MAX_STAGES);
   const uint32_t kc_ready_a = smem_u32(kc_ready);
   volatile int* kc_fail = (volatile int*)(kc_ready + 1);   // a k-transform tile copy gave up
+  volatile int* kc_copies = (volatile int*)(kc_ready + 2);  // tile copies issued, seen landed
   const uint32_t sbase = smem_u32(sm);
   auto full = [&](int s) { return smem_u32(&bars[s]); };
   auto empty = [&](int s) { return smem_u32(&bars[S + s]); };
@@ -343,6 +347,8 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
     *issued = 0;
     *kc_ready = 0;
     *kc_fail = 0;
+    kc_copies[0] = 0;
+    kc_copies[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -644,7 +650,7 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
       bool unit_ok = true;
       for (int u = first; u < nu && unit_ok; u += G, ++kc_phase) {
         unit_ok = kc_unit<N>(p, kc_tile, kc_bar, kc_phase & 1u, u % p.nc, s * (OP_M / KC_XW) + u / p.nc, tid, labort,
-                             kc_fail);
+                             kc_fail, kc_copies);
         if (!unit_ok) break;
         // the unit's Phi' stores precede the barrier; one fence by the thread
         // that publishes the unit
@@ -668,6 +674,12 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
     for (int it = *consumed; it < *issued; ++it) {
       const unsigned long long t0 = gtime();
       while (!mbar_try(full(it % S), (uint32_t)(it / S) & 1u) && gtime() - t0 < DRAIN_NS) {
+      }
+    }
+    // and a k-transform tile copy whose wait gave up (phase = copies issued - 1)
+    if (kc_copies[0] > kc_copies[1]) {
+      const unsigned long long t0 = gtime();
+      while (!mbar_try(kc_bar, (uint32_t)(kc_copies[0] - 1) & 1u) && gtime() - t0 < DRAIN_NS) {
       }
     }
   }
