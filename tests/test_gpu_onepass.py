@@ -44,6 +44,25 @@ def test_schedules_match_oracle(kw, sched):
     sysg.close()
 
 
+@pytest.mark.parametrize("kw", [
+    dict(seed=94, n_alpha=1, nk=(4, 4, 4), n_bands=80, nx=(6, 6, 4), n_proj=2),    # 2 Nb = 160: two M tiles
+    dict(seed=95, n_alpha=2, nk=(2, 3, 2), n_bands=8, nx=(5, 4, 3), n_proj=1),     # any mesh, odd grid
+])
+def test_row_major_two_pass_other_shapes(kw):
+    """The row-major two-pass schedule takes shapes the one-pass kernel does
+    not: several 128-row M tiles of grid->band (q blocks beyond 2 Nb are
+    zero-filled by the tensor map), non-cubic meshes and odd grids."""
+    s = S.tiny_system(**kw)
+    psi = S.complex_normal(np.random.default_rng(kw["seed"]), (2, s.dim))
+    sysg = bse.System(s, precision="split_bf16", max_vec=2)
+    sysg.set_schedule("two_pass_rowmajor")
+    out = sysg.apply_h(psi)
+    ref = O.apply_h(s, psi)
+    for v in range(2):
+        close("two_pass_rowmajor/seed%d/v%d" % (kw["seed"], v), out[v], ref[v], "split_bf16")
+    sysg.close()
+
+
 def test_one_pass_several_vectors_and_fallback():
     """N_alpha = 1: up to 8 vectors in one pass; 9 fall back to the two-pass step."""
     s = S.tiny_system(99, n_alpha=1, nk=(4, 4, 4), n_bands=16, nx=(8, 8, 4), n_proj=2)
